@@ -1,0 +1,371 @@
+"""Benchmark: Fourier-accelerated Landau gauge fixing of a 64^4 SU(3) configuration on GB300.
+
+Metric: site-iterations/s and time-to-theta < 1e-15 at 64^4, mixed FP32->FP64 vs FP64, and the HBM
+roofline of the kernels.
+
+A step is one complete gauge fixing (Algorithm 1 of Cardoso et al., run until theta < 1e-15) of the
+64^4 configuration (eps = 0.6, seed 4; links 9.66 GB in double precision), with the mixed-precision
+schedule: float links, FFTs and updates with double reductions until theta <= 1e-8, then the double
+handover and double precision to theta < 1e-15. The input stays resident in HBM and is never
+modified (load -> iterate -> store into a separate output buffer), so every step repeats the same
+work. `value` = V * iterations / time (site-iterations per second over whole fixes); `ms_per_step`
+is the time to theta < 1e-15. Beside it: the same field fixed in plain FP64, per-kernel device times
+from CUDA events recorded on the working stream during the timed steps, the end-to-end figure through
+the C ABI from pinned host buffers (copies included), and the CPU oracle timed on a bounded sample.
+
+Multi-GPU (torchrun): one independent replica per rank (seed 4 + rank); no collective on the data
+path; value = all ranks' site-iterations / max over ranks of the time.
+
+--impl reference runs the FP64 CPU oracle on the host cores instead (rank 0 only): each step is one
+iteration of Algorithm 1 on the same 64^4 configuration.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "site-iterations/s & time-to-θ≤1e-15 at 64^4, FP32→FP64 vs FP64; % HBM peak"
+UNIT = "site-iterations/s"
+
+# Nominal FP64 rate derived from the unit counts and clock: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop
+# x 2.07 GHz = 1.259 TFLOP/s (GB300 FP64 is 1.25 TFLOP/s nominal).
+FP64_FLOP_PER_CLK = 152 * 2 * 2
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        p = json.load(open(path))
+        return float(p["hbm_gbs"]), float(p.get("sm_max_mhz", 2070.0)), "measured"
+    return 6800.0, 2070.0, "fallback"
+
+
+def algorithmic(kernel, dims):
+    """Algorithmic bytes and flops per launch of each kernel (each datum counted once).
+    es = bytes per complex number; flops counted in the kernel's own precision."""
+    V = int(np.prod(dims))
+    name, prec = kernel.rsplit(".", 1)
+    es = 16 if prec == "f64" else 8
+    nx, ny, nz, nt = dims
+    lg = {k: np.log2(n) for k, n in zip("xyzt", dims)}
+    table = {
+        # 4 links read (the backward neighbours are the same data), 4 packed Delta written
+        "delta_theta": ((36 + 4) * es, 190),
+        # read + write 4 packed fields; FFT flops 5 N log2 N per field per axis per direction
+        "fft_xy_fwd": (8 * es, 4 * 5 * (lg["x"] + lg["y"])),
+        "fft_xy_inv": (8 * es, 4 * 5 * (lg["x"] + lg["y"])),
+        "fft_x_fwd": (8 * es, 4 * 5 * lg["x"]), "fft_x_inv": (8 * es, 4 * 5 * lg["x"]),
+        "fft_y_fwd": (8 * es, 4 * 5 * lg["y"]), "fft_y_inv": (8 * es, 4 * 5 * lg["y"]),
+        "fft_z_fwd": (8 * es, 4 * 5 * lg["z"]), "fft_z_inv": (8 * es, 4 * 5 * lg["z"]),
+        "fft_zt_filter": (8 * es, 4 * (2 * 5 * (lg["z"] + lg["t"]) + 6)),
+        "fft_t_filter": (8 * es, 4 * (2 * 5 * lg["t"] + 6)),
+        # packed Delta-tilde read, g written
+        "gauge_g": ((4 + 9) * es, 160),
+        # links read and written, g read (neighbours are the same data); 8 SU(3) products
+        "gauge_update": ((36 + 36 + 9) * es, 8 * 216),
+        "gauge_update_accumulate": ((36 + 36 + 9 + 18) * es, 9 * 216),
+        "reunitarize": (5 * 9 * 2 * 8, 5 * 170),
+        "gacc_to_double": (9 * 8 + 9 * 16, 170),
+        "handover_transform": (36 * 16 * 2 + 9 * 16, 8 * 216),
+        "to_planes": (36 * 16 + 36 * es, 0),
+        "from_planes": (36 * es + 36 * 16, 0),
+        "set_identity": (9 * 8, 0),
+    }
+    b, f = table[name]
+    return b * V, f * V, prec
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args, dims, rank, ws):
+    """The FP64 CPU oracle on the host cores: each step is one iteration of Algorithm 1 on the 64^4
+    configuration (the untimed part loads the configuration and its initial Delta)."""
+    if rank != 0:
+        return
+    import oracle
+    import synth
+    cores = os.cpu_count()
+    U = synth.config(dims, args.seed, args.eps)
+    V = int(np.prod(dims))
+    for _ in range(args.warmup):
+        U, _, _, _, _ = oracle.fix(U, 0.08, 0.0, 1)
+    t0 = time.perf_counter()
+    U, it, th, F, _ = oracle.fix(U, 0.08, 0.0, args.steps)
+    dt = time.perf_counter() - t0
+    # oracle.fix also evaluates Delta/theta/F of the input once before its loop (a 1/(K+1) share)
+    value = V * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_of(args, dims, "fp64 CPU oracle"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d iterations of Algorithm 1 on the %s configuration" % (args.steps, "x".join(map(str, dims)))},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_of(args, dims, path):
+    return {"workload": "%s SU(3) lattice, U=h exp(i eps A) h^+(x+mu), eps=%g, seed %d; alpha=0.08, "
+                        "theta<1e-15; %s" % ("^".join(["64", "4"]) if dims == (64, 64, 64, 64) else "x".join(map(str, dims)),
+                                             args.eps, args.seed, path),
+            "lattice": list(dims), "precision": args.precision, "theta_switch": args.theta_switch,
+            "step": "one complete gauge fixing (Algorithm 1 until theta < 1e-15)",
+            "l2": "no flush: links 9.66 GB per step >> 129 MB L2" if np.prod(dims) >= 2 ** 20 else "small lattice",
+            "parallelism": "replicas"}
+
+
+def cpu_baseline(dims, args, V_gpu):
+    """The oracle as it stands on the host cores, on a bounded sample: one iteration of Algorithm 1 on
+    the same configuration (falls back to a 32^4 configuration when host memory is short)."""
+    import oracle
+    import synth
+    need = int(np.prod(dims)) * 4 * 144 * 3.2
+    avail = 0
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable"):
+                avail = int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    cdims = dims if avail > need else (32, 32, 32, 32)
+    U = synth.config(cdims, args.seed, args.eps)
+    Vc = int(np.prod(cdims))
+    t0 = time.perf_counter()
+    oracle.fix(U, 0.08, 0.0, 1)
+    dt = time.perf_counter() - t0
+    return {"value": Vc / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "one iteration of Algorithm 1 (plus the initial Delta/theta/F) on the %s configuration, "
+                      "%.1f s" % ("x".join(map(str, cdims)), dt)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="lgf", choices=["lgf", "reference"])
+    ap.add_argument("--lattice", type=int, nargs=4, default=[64, 64, 64, 64])
+    ap.add_argument("--eps", type=float, default=0.6)
+    ap.add_argument("--seed", type=int, default=4)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "fp32"])
+    ap.add_argument("--theta-switch", type=float, default=1e-8)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison fix")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    assert args.warmup >= 3 or args.impl == "reference", "at least 3 warm-up steps"
+    dims = tuple(args.lattice)
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, dims, rank, ws)
+        return
+
+    import torch
+    import synth
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import paper_1210_8018_gb300 as lgf
+
+    V = int(np.prod(dims))
+    seed = args.seed + rank
+    host = torch.empty(synth.links_shape(dims), dtype=torch.complex128).pin_memory()
+    synth.config(dims, seed, args.eps, out=host.numpy())
+    U_in = host.to("cuda", non_blocking=False)
+    U_out = torch.empty_like(U_in)
+    lat = lgf.Lattice(dims)
+    stream = torch.cuda.current_stream()
+    lat.set_stream(stream)
+
+    def one_fix(prec):
+        lat.load(U_in, prec)
+        r = lat.iterate(1 << 30, 0.08, 1e-15, theta_switch=args.theta_switch)
+        lat.store(U_out)
+        return r
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up (untimed)
+    for _ in range(args.warmup):
+        r = one_fix(args.precision)
+    lat.enable_timing(True)
+    lat.kernel_times()  # reset counters
+    barrier()
+    iters = []
+    with ClockSampler(local) as clk:
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            r = one_fix(args.precision)
+            iters.append(r["iters"])
+            if not r["converged"]:
+                raise SystemExit("fix did not converge: %r" % r)
+        ev1.record(stream)
+        barrier()
+    ktimes = lat.kernel_times()
+    ms = ev0.elapsed_time(ev1)
+    t_max = ms
+    site_iters = V * sum(iters)
+    if ws > 1:
+        t = torch.tensor([ms, float(site_iters)], device="cuda", dtype=torch.float64)
+        tm = t.clone()
+        torch.distributed.all_reduce(tm[:1], op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
+        t_max, site_iters = float(tm[0]), float(t[1])
+    value = site_iters / (t_max / 1e3)
+    lat.enable_timing(False)
+
+    # plain FP64 on the same field (1 warm-up, 1 timed)
+    fp64 = None
+    if not args.no_fp64 and args.precision != "fp64":
+        one_fix("fp64")
+        barrier()
+        lat.enable_timing(True)
+        lat.kernel_times()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r64 = one_fix("fp64")
+        e1.record(stream)
+        barrier()
+        k64 = lat.kernel_times()
+        lat.enable_timing(False)
+        t64 = e0.elapsed_time(e1)
+        fp64 = {"time_to_theta_s": t64 / 1e3, "iters": r64["iters"], "site_iterations_per_s": V * r64["iters"] / (t64 / 1e3),
+                "theta": r64["theta"], "F": r64["F"],
+                "kernels_ms": {k: round(v[1], 3) for k, v in sorted(k64.items(), key=lambda kv: -kv[1][1])}}
+
+    # roofline of every kernel; the dominant kernel (largest share of the timed steps) is reported
+    hbm, sm_max, which = peaks()
+    clocks = clk.summary()
+    fp64_peak = FP64_FLOP_PER_CLK * (clocks["sm_mhz"] or sm_max) * 1e6
+    kernels = {}
+    total_ms = sum(v[1] for v in ktimes.values())
+    for name, (n, kms) in ktimes.items():
+        b, f, prec = algorithmic(name, dims)
+        per = kms / n / 1e3
+        gbs = b / per / 1e9
+        d = {"launches": n, "ms_total": round(kms, 3), "share": round(kms / total_ms, 4),
+             "ms_per_launch": round(kms / n, 4), "GB_s": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4)}
+        if prec == "f64" and f > 0:
+            d["fp64_tflops"] = round(f / per / 1e12, 4)
+            d["fp64_frac"] = round(f / per / fp64_peak, 4)
+        kernels[name] = d
+    dom = max(kernels, key=lambda k: kernels[k]["ms_total"])
+    dk = kernels[dom]
+    b, f, prec = algorithmic(dom, dims)
+    per = dk["ms_per_launch"] / 1e3
+    if prec == "f64" and dk.get("fp64_frac", 0) > dk["hbm_frac"]:
+        roof = {"bound": "alu", "achieved": round(f / per / 1e12, 4), "peak": round(fp64_peak / 1e12, 4),
+                "unit": "TFLOP/s", "frac": round(f / per / fp64_peak, 4), "traffic": None,
+                "kernel": dom, "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x median SM clock"}
+    else:
+        roof = {"bound": "hbm", "achieved": round(b / per / 1e9, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(b / per / 1e9 / hbm, 4), "traffic": None, "kernel": dom,
+                "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % which}
+
+    # end to end through the C ABI from pinned host buffers (H2D + fix + D2H inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        work = torch.empty_like(host).pin_memory()
+        times = []
+        for rep in range(2):
+            work.copy_(host)
+            barrier()
+            t0 = time.perf_counter()
+            r = lat.fix(work.numpy(), 0.08, 1e-15, args.precision, theta_switch=args.theta_switch)
+            dt = time.perf_counter() - t0
+            if rep > 0:
+                times.append((dt, r["iters"]))
+        dt, it = times[0]
+        nbytes = 4 * V * 144
+        e2e = {"value": V * it / dt, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+               "time_to_theta_s": dt, "step": "one lgf_fix call on pinned host links"}
+
+    if rank == 0:
+        gpu_launches = sum(v[0] for v in ktimes.values())
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": {"mixed": "f32+f64", "fp64": "f64", "fp32": "f32"}[args.precision],
+                "data": "synthetic", "config": config_of(args, dims, args.precision),
+                "iters_per_step": iters[0], "time_to_theta_s": {args.precision: t_max / args.steps / 1e3},
+                "roofline": roof, "gpu_launches": gpu_launches, "clocks": clocks, "e2e": e2e,
+                "kernels": kernels}
+        if fp64:
+            line["time_to_theta_s"]["fp64"] = fp64["time_to_theta_s"]
+            line["fp64"] = fp64
+        if not args.no_cpu:
+            line["cpu_baseline"] = cpu_baseline(dims, args, V)
+        print(json.dumps(line), flush=True)
+    lat.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

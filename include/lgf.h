@@ -1,0 +1,151 @@
+/*
+ * lgf.h -- C ABI of the GB300 (sm_103a) library for Fourier-accelerated steepest-descent Landau gauge
+ * fixing of SU(3) lattice gauge fields (Cardoso, Silva, Oliveira, Bicudo, "GPU implementation of a
+ * Landau gauge fixing algorithm", Lattice 2012).
+ *
+ * The method maximises F_U[g] (Eq. 1) on the gauge orbit of U. Each iteration of Algorithm 1 computes
+ * Delta(x) (Eqs. 3, 5), theta (Eq. 4) and F, Fourier-filters Delta with p^2_max/p^2 (Eq. 2), forms
+ * g(x) = SU(3)-projection of [1 + (alpha/2) Delta-tilde(x)] and applies U_mu(x) -> g(x)U_mu(x)g^+(x+mu).
+ * The loop stops when theta < eps (Algorithm 1: "while theta >= eps").
+ *
+ * Conventions shared by every entry point
+ *   Lattice: Nx, Ny, Nz, Nt, periodic; V = Nx*Ny*Nz*Nt; site s = x + Nx*(y + Ny*(z + Nz*t)).
+ *   Links (caller-owned): 4*V*9 complex doubles (re, im interleaved), index ((mu*V + s)*3 + i)*3 + j
+ *     for direction mu in {x,y,z,t}, row i, column j; i.e. a contiguous complex128 array of shape
+ *     (4, Nt, Nz, Ny, Nx, 3, 3). 144 bytes per link, 4*V*144 bytes in all.
+ *   Site matrix fields (Delta, Delta-tilde, g): V*9 complex doubles, index (s*3 + i)*3 + j.
+ *   Pointers may be device pointers (CUDA global memory of the context's device) or host pointers
+ *     (pageable or pinned); the library detects which and copies host data through its own device
+ *     buffers. Device pointers must be 16-byte aligned.
+ *   Streams: work is issued on the stream given to lgf_set_stream (default: a stream the context
+ *     creates). Every call returns only after its results are complete (it synchronizes that stream).
+ *   Errors: every call returns an lgf_status; outputs are written only when the call returns LGF_OK
+ *     (or LGF_ENOCONV, see lgf_fix). After a CUDA error the context is poisoned and every later call
+ *     returns LGF_ECUDA. lgf_last_error gives a message for the last failing call.
+ *   Threads: a context must not be used by two threads at once; distinct contexts are independent.
+ *   Ownership: the context owns all its device workspaces; the caller owns every buffer it passes.
+ */
+#ifndef LGF_H
+#define LGF_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lgf_ctx lgf_ctx;
+
+typedef enum {
+  LGF_OK = 0,
+  LGF_EINVAL = 1,     /* bad argument: size, pointer, option or call order                  */
+  LGF_ENOMEM = 2,     /* a device or pinned allocation failed                                */
+  LGF_ECUDA = 3,      /* a CUDA call or kernel failed; the context is poisoned               */
+  LGF_ENOCONV = 4,    /* the iteration limit was reached before theta < eps                  */
+  LGF_ENONFINITE = 5  /* theta or F became NaN or infinite (e.g. non-finite input links)     */
+} lgf_status;
+
+typedef enum {
+  LGF_FP64 = 0,  /* every step in double precision                                               */
+  LGF_MIXED = 1, /* float links, FFTs and updates (double reductions) until theta <= theta_switch,
+                    then a double-precision handover and double precision to theta < eps         */
+  LGF_FP32 = 2   /* float links, FFTs and updates throughout (double reductions)                 */
+} lgf_precision;
+
+typedef struct {
+  int precision;       /* lgf_precision; default LGF_FP64                                          */
+  double theta_switch; /* LGF_MIXED: theta at which the float stage hands over; default 1e-8       */
+  int reunit_period;   /* float stages: links and accumulated transformation reprojected to SU(3)
+                          in double precision every this many iterations; default 16               */
+  int max_iter;        /* iteration limit; default 100000                                          */
+  double *history;     /* optional host buffer: history[2k] = theta, history[2k+1] = F after k
+                          updates (k = 0 is the input), for k < history_len                         */
+  int history_len;
+} lgf_options;
+
+/* Fill *opt with the defaults listed above. */
+void lgf_default_options(lgf_options *opt);
+
+/* Create a context for an Nx x Ny x Nz x Nt lattice on the current CUDA device. Every extent must be
+ * >= 2 and a product of the primes 2, 3 and 5, and at most 1024. Device memory is allocated lazily by
+ * the first call that needs it. Returns LGF_EINVAL for unsupported extents, LGF_ECUDA if no device. */
+lgf_status lgf_create(int Nx, int Ny, int Nz, int Nt, lgf_ctx **out);
+
+/* Release every resource of the context (NULL is accepted). */
+void lgf_destroy(lgf_ctx *ctx);
+
+/* Message for the last failing call on this context (a static string if ctx is NULL). */
+const char *lgf_last_error(const lgf_ctx *ctx);
+
+/* Issue all later work on `stream` (a cudaStream_t; NULL restores the context's own stream, which is
+ * non-blocking; pass cudaStreamLegacy to use the legacy default stream). */
+lgf_status lgf_set_stream(lgf_ctx *ctx, void *stream);
+
+/* Algorithm 1 in full: fix the links in place to Landau gauge.
+ *   links      in/out, the layout above (device or host pointer)
+ *   alpha      step size (the paper uses 0.08, after Davies et al.)
+ *   eps        stop when theta < eps (the paper: 1e-15)
+ *   opt        NULL for the defaults
+ *   theta_out, F_out, iters_out   final theta (Eq. 4), F (Eq. 1 at g = 1) and the number of gauge
+ *              updates applied (0 if theta < eps on input); any may be NULL
+ * Returns LGF_OK on convergence; LGF_ENOCONV when max_iter updates did not reach theta < eps (the
+ * links and outputs then hold the last state); LGF_ENONFINITE if theta or F became non-finite. */
+lgf_status lgf_fix(lgf_ctx *ctx, double *links, double alpha, double eps, const lgf_options *opt,
+                   double *theta_out, double *F_out, int *iters_out);
+
+/* theta (Eq. 4), F (Eq. 1 at g = 1) and the average plaquette (1/3) Re Tr of the 1x1 loop, averaged
+ * over sites and the six planes, of the given links. Any output may be NULL. */
+lgf_status lgf_measure(lgf_ctx *ctx, const double *links, double *theta, double *F, double *plaq);
+
+/* ---- Session interface: the loop of Algorithm 1 split into load / iterate / store, so that a
+ * caller can run a fixed number of iterations, inspect the state, or time the loop. lgf_fix is
+ * lgf_load + lgf_iterate + lgf_store. ---- */
+
+/* Load links into the context's working state at the given precision and compute Delta, theta and F
+ * of the input (Algorithm 1, first line). Resets the iteration count. With LGF_MIXED the input is kept
+ * in double precision for the handover. */
+lgf_status lgf_load(lgf_ctx *ctx, const double *links, int precision);
+
+/* Run at most max_new iterations of the loop of Algorithm 1 on the working state, stopping early when
+ * theta < eps (and, with LGF_MIXED, handing over to double precision at theta_switch). theta/F/iters
+ * report the state after the call (iters counts all updates since lgf_load). opt supplies
+ * theta_switch, reunit_period and history; NULL for the defaults. Returns LGF_OK when theta < eps,
+ * LGF_ENOCONV when the limit stopped it first, LGF_ENONFINITE on a non-finite theta or F. */
+lgf_status lgf_iterate(lgf_ctx *ctx, int max_new, double alpha, double eps, const lgf_options *opt,
+                       double *theta, double *F, int *iters);
+
+/* Write the working state back to links (double precision, the layout above). With LGF_MIXED still in
+ * its float stage, the links are rebuilt as G(x) U0_mu(x) G^+(x+mu) in double precision from the
+ * saved input U0 and the accumulated transformation G, so they stay gauge-equivalent to the input. */
+lgf_status lgf_store(lgf_ctx *ctx, double *links);
+
+/* ---- Single steps of one iteration, on caller buffers in the layouts above (used to check each
+ * step against a reference implementation; not needed to fix a gauge). All run in double precision
+ * unless `precision` says LGF_FP32. ---- */
+
+/* Eqs. 3-5 and Eq. 1: Delta(x) (V*9 complex, out), theta and F of links. */
+lgf_status lgf_delta(lgf_ctx *ctx, const double *links, double *delta, double *theta, double *F,
+                     int precision);
+
+/* Algorithm 1, FFT block: Delta-tilde = F^-1[ (p^2_max/p^2) F[Delta] ] / V, zero mode set to 0.
+ * delta must be anti-Hermitian and traceless at every site (as Eq. 5 makes it); only its upper
+ * triangle and diagonal imaginary parts are read. dtilde (out) is written in full. */
+lgf_status lgf_filter(lgf_ctx *ctx, const double *delta, double *dtilde, int precision);
+
+/* Eq. 2 to first order plus projection: g(x) = SU(3)-projection of [1 + (alpha/2) Delta-tilde(x)]
+ * (Gram-Schmidt on rows 1-2, row 3 = conj(row1 x row2)). Same input rule as lgf_filter. */
+lgf_status lgf_gauge(lgf_ctx *ctx, const double *dtilde, double alpha, double *g, int precision);
+
+/* Algorithm 1: U_mu(x) -> g(x) U_mu(x) g^+(x + mu) for all x, mu (links in/out, g in). */
+lgf_status lgf_update(lgf_ctx *ctx, double *links, const double *g, int precision);
+
+/* ---- Timing of the loop's kernels: when enabled, lgf_iterate brackets every kernel launch with CUDA
+ * events on the working stream and accumulates per-kernel device time. ---- */
+lgf_status lgf_enable_timing(lgf_ctx *ctx, int enable);
+/* Copy up to `cap` entries: name[i] (static strings), launches[i], total device milliseconds ms[i];
+ * *count gets the number of kernels with timing data. Resets the counters. */
+lgf_status lgf_kernel_times(lgf_ctx *ctx, const char **name, long *launches, double *ms, int cap,
+                            int *count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LGF_H */

@@ -1,0 +1,241 @@
+"""Fourier-accelerated steepest-descent Landau gauge fixing of SU(3) lattice gauge fields on GB300.
+
+A thin Python binding over the C ABI of liblgf.so (include/lgf.h): it only marshals arguments. Every
+step of the iteration (Cardoso, Silva, Oliveira, Bicudo, Lattice 2012, Algorithm 1) runs in the CUDA
+kernels of that library; there is no Python or CPU fallback, and importing this module fails if the
+library is missing.
+
+Links are complex128 arrays of shape (4, Nt, Nz, Ny, Nx, 3, 3) (direction, site with x fastest, row,
+column): torch tensors on the GPU (used in place) or numpy arrays / CPU tensors (copied through the
+library's device buffers).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "liblgf.so")
+
+if not os.path.exists(_SO):
+    raise ImportError("liblgf.so is not built; run __graft_entry__.build() (needs nvcc for sm_103a)")
+_lib = ctypes.CDLL(_SO)
+
+LGF_OK, LGF_EINVAL, LGF_ENOMEM, LGF_ECUDA, LGF_ENOCONV, LGF_ENONFINITE = range(6)
+FP64, MIXED, FP32 = 0, 1, 2
+_PREC = {"fp64": FP64, "mixed": MIXED, "fp32": FP32, FP64: FP64, MIXED: MIXED, FP32: FP32}
+_STATUS = {0: "LGF_OK", 1: "LGF_EINVAL", 2: "LGF_ENOMEM", 3: "LGF_ECUDA", 4: "LGF_ENOCONV", 5: "LGF_ENONFINITE"}
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("theta_switch", ctypes.c_double), ("reunit_period", ctypes.c_int),
+                ("max_iter", ctypes.c_int), ("history", ctypes.POINTER(ctypes.c_double)),
+                ("history_len", ctypes.c_int)]
+
+
+_vp, _d, _i = ctypes.c_void_p, ctypes.c_double, ctypes.c_int
+_P = ctypes.POINTER
+_SIGS = {
+    "lgf_default_options": (None, [_P(Options)]),
+    "lgf_create": (_i, [_i, _i, _i, _i, _P(_vp)]),
+    "lgf_destroy": (None, [_vp]),
+    "lgf_last_error": (ctypes.c_char_p, [_vp]),
+    "lgf_set_stream": (_i, [_vp, _vp]),
+    "lgf_fix": (_i, [_vp, _vp, _d, _d, _P(Options), _P(_d), _P(_d), _P(_i)]),
+    "lgf_measure": (_i, [_vp, _vp, _P(_d), _P(_d), _P(_d)]),
+    "lgf_load": (_i, [_vp, _vp, _i]),
+    "lgf_iterate": (_i, [_vp, _i, _d, _d, _P(Options), _P(_d), _P(_d), _P(_i)]),
+    "lgf_store": (_i, [_vp, _vp]),
+    "lgf_delta": (_i, [_vp, _vp, _vp, _P(_d), _P(_d), _i]),
+    "lgf_filter": (_i, [_vp, _vp, _vp, _i]),
+    "lgf_gauge": (_i, [_vp, _vp, _d, _vp, _i]),
+    "lgf_update": (_i, [_vp, _vp, _vp, _i]),
+    "lgf_enable_timing": (_i, [_vp, _i]),
+    "lgf_kernel_times": (_i, [_vp, _P(ctypes.c_char_p), _P(ctypes.c_long), _P(_d), _i, _P(_i)]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+class LgfError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (_STATUS.get(status, status), msg))
+        self.status = status
+
+
+def library_path():
+    return _SO
+
+
+_CUDA_STREAM_LEGACY = 1  # cudaStreamLegacy
+
+
+def _torch_stream_handle():
+    """Raw handle of torch's current CUDA stream (the legacy default stream as cudaStreamLegacy)."""
+    import torch
+    h = torch.cuda.current_stream().cuda_stream
+    return h if h else _CUDA_STREAM_LEGACY
+
+
+def _ptr(a):
+    """Device or host address of a complex128 C-contiguous torch tensor or numpy array."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.complex128 or not a.flags.c_contiguous:
+            raise ValueError("numpy arrays must be complex128 and C-contiguous")
+        return a.ctypes.data
+    import torch
+    if isinstance(a, torch.Tensor):
+        if a.dtype != torch.complex128 or not a.is_contiguous():
+            raise ValueError("tensors must be complex128 and contiguous")
+        return a.data_ptr()
+    raise TypeError("expected a numpy array or a torch tensor")
+
+
+def dims_of(U):
+    nt, nz, ny, nx = tuple(U.shape[1:5])
+    return (int(nx), int(ny), int(nz), int(nt))
+
+
+class Lattice:
+    """A gauge-fixing context for one lattice shape (Nx, Ny, Nz, Nt) on the current CUDA device."""
+
+    def __init__(self, dims):
+        self.dims = tuple(int(d) for d in dims)
+        h = ctypes.c_void_p()
+        st = _lib.lgf_create(*self.dims, ctypes.byref(h))
+        if st != LGF_OK:
+            raise LgfError(st, _lib.lgf_last_error(None).decode())
+        self._h = h
+        self._stream = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.lgf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _bind(self, *arrays):
+        """Order the library's work after torch's: unless set_stream() chose a stream, issue on torch's
+        current stream whenever a CUDA tensor is passed."""
+        if self._stream is not None:
+            return
+        for a in arrays:
+            if not isinstance(a, np.ndarray) and getattr(a, "is_cuda", False):
+                self._check(_lib.lgf_set_stream(self._h, _torch_stream_handle()))
+                return
+
+    def _check(self, st, allow=(LGF_OK,)):
+        if st not in allow:
+            raise LgfError(st, _lib.lgf_last_error(self._h).decode())
+        return st
+
+    def set_stream(self, stream):
+        """Issue work on a torch.cuda.Stream (or a raw cudaStream_t as int); None = own stream."""
+        raw = None
+        if stream is not None:
+            raw = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+            raw = raw if raw else _CUDA_STREAM_LEGACY
+        self._stream = stream
+        self._check(_lib.lgf_set_stream(self._h, raw))
+
+    @staticmethod
+    def options(precision="fp64", theta_switch=1e-8, reunit_period=16, max_iter=100000, history=None):
+        o = Options()
+        _lib.lgf_default_options(ctypes.byref(o))
+        o.precision = _PREC[precision]
+        o.theta_switch = theta_switch
+        o.reunit_period = reunit_period
+        o.max_iter = max_iter
+        if history is not None:
+            o.history = history.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            o.history_len = history.shape[0]
+        return o
+
+    def fix(self, U, alpha=0.08, eps=1e-15, precision="fp64", max_iter=100000, theta_switch=1e-8,
+            reunit_period=16, history_len=0):
+        """Algorithm 1: fix U in place. Returns dict(theta, F, iters, converged, history)."""
+        hist = np.zeros((history_len, 2), dtype=np.float64) if history_len > 0 else None
+        o = self.options(precision, theta_switch, reunit_period, max_iter, hist)
+        th, F, it = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+        self._bind(U)
+        st = self._check(_lib.lgf_fix(self._h, _ptr(U), alpha, eps, ctypes.byref(o), ctypes.byref(th),
+                                      ctypes.byref(F), ctypes.byref(it)), (LGF_OK, LGF_ENOCONV))
+        out = dict(theta=th.value, F=F.value, iters=it.value, converged=(st == LGF_OK))
+        if hist is not None:
+            out["history"] = hist[:min(it.value + 1, history_len)]
+        return out
+
+    def measure(self, U):
+        th, F, pl = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        self._bind(U)
+        self._check(_lib.lgf_measure(self._h, _ptr(U), ctypes.byref(th), ctypes.byref(F), ctypes.byref(pl)))
+        return dict(theta=th.value, F=F.value, plaquette=pl.value)
+
+    # session interface
+    def load(self, U, precision="fp64"):
+        self._bind(U)
+        self._check(_lib.lgf_load(self._h, _ptr(U), _PREC[precision]))
+
+    def iterate(self, max_new, alpha=0.08, eps=1e-15, theta_switch=1e-8, reunit_period=16, history_len=0):
+        hist = np.zeros((history_len, 2), dtype=np.float64) if history_len > 0 else None
+        o = self.options("fp64", theta_switch, reunit_period, 0, hist)
+        th, F, it = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+        st = self._check(_lib.lgf_iterate(self._h, int(max_new), alpha, eps, ctypes.byref(o), ctypes.byref(th),
+                                          ctypes.byref(F), ctypes.byref(it)), (LGF_OK, LGF_ENOCONV))
+        out = dict(theta=th.value, F=F.value, iters=it.value, converged=(st == LGF_OK))
+        if hist is not None:
+            out["history"] = hist
+        return out
+
+    def store(self, U):
+        self._bind(U)
+        self._check(_lib.lgf_store(self._h, _ptr(U)))
+
+    # single steps
+    def delta(self, U, out, precision="fp64"):
+        th, F = ctypes.c_double(), ctypes.c_double()
+        self._bind(U, out)
+        self._check(_lib.lgf_delta(self._h, _ptr(U), _ptr(out), ctypes.byref(th), ctypes.byref(F),
+                                   _PREC[precision]))
+        return th.value, F.value
+
+    def filter(self, delta, out, precision="fp64"):
+        self._bind(delta, out)
+        self._check(_lib.lgf_filter(self._h, _ptr(delta), _ptr(out), _PREC[precision]))
+
+    def gauge(self, dtilde, alpha, out, precision="fp64"):
+        self._bind(dtilde, out)
+        self._check(_lib.lgf_gauge(self._h, _ptr(dtilde), float(alpha), _ptr(out), _PREC[precision]))
+
+    def update(self, U, g, precision="fp64"):
+        self._bind(U, g)
+        self._check(_lib.lgf_update(self._h, _ptr(U), _ptr(g), _PREC[precision]))
+
+    # timing
+    def enable_timing(self, on=True):
+        self._check(_lib.lgf_enable_timing(self._h, 1 if on else 0))
+
+    def kernel_times(self):
+        cap = 32
+        names = (ctypes.c_char_p * cap)()
+        launches = (ctypes.c_long * cap)()
+        ms = (ctypes.c_double * cap)()
+        n = ctypes.c_int()
+        self._check(_lib.lgf_kernel_times(self._h, names, launches, ms, cap, ctypes.byref(n)))
+        return {names[i].decode(): (launches[i], ms[i]) for i in range(min(n.value, cap))}
+
+
+def fix(U, alpha=0.08, eps=1e-15, precision="fp64", **kw):
+    """Fix the links U (complex128, (4, Nt, Nz, Ny, Nx, 3, 3)) to Landau gauge in place."""
+    with Lattice(dims_of(U)) as lat:
+        return lat.fix(U, alpha, eps, precision, **kw)

@@ -1,0 +1,1033 @@
+// lgf.cu -- host side of the Landau-gauge-fixing library: context, FFT pass planning, the loop of
+// Algorithm 1 (Cardoso et al., Lattice 2012) with device-side loop control, the mixed-precision
+// handover, and the C ABI declared in include/lgf.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "../../include/lgf.h"
+#include "fft.cuh"
+#include "mixed_kernels.cuh"
+#include "site_kernels.cuh"
+
+using namespace lgf;
+
+namespace {
+
+constexpr int NT = 256;  // threads per block of the per-site kernels
+
+enum KernelId {
+  KID_DELTA = 0,
+  KID_FFT_XY_FWD,
+  KID_FFT_X_FWD,
+  KID_FFT_Y_FWD,
+  KID_FFT_Z_FWD,
+  KID_FFT_ZT_FILTER,
+  KID_FFT_T_FILTER,
+  KID_FFT_Z_INV,
+  KID_FFT_Y_INV,
+  KID_FFT_X_INV,
+  KID_FFT_XY_INV,
+  KID_GAUGE,
+  KID_UPDATE,
+  KID_UPDATE_ACC,
+  KID_REUNIT,
+  KID_GACC_TO_DOUBLE,
+  KID_TRANSFORM_FROM,
+  KID_TO_PLANES,
+  KID_FROM_PLANES,
+  KID_SET_IDENTITY,
+  KID_COUNT
+};
+// kernel names; the float instance of a kernel is reported with the suffix .f32, the double with .f64
+const char *kKernelBase[KID_COUNT] = {"delta_theta",   "fft_xy_fwd",    "fft_x_fwd",      "fft_y_fwd",
+                                      "fft_z_fwd",     "fft_zt_filter", "fft_t_filter",   "fft_z_inv",
+                                      "fft_y_inv",     "fft_x_inv",     "fft_xy_inv",     "gauge_g",
+                                      "gauge_update",  "gauge_update_accumulate", "reunitarize",
+                                      "gacc_to_double", "handover_transform", "to_planes", "from_planes",
+                                      "set_identity"};
+std::string kKernelNames[2 * KID_COUNT];
+template <typename T> int kid(int k) { return std::is_same<T, float>::value ? k + KID_COUNT : k; }
+
+struct Pass {
+  PassDesc d;
+  int kid;
+  size_t smem;
+  int threads;
+};
+
+template <typename T> struct State {
+  T *U = nullptr;  // links, planes
+  T *P = nullptr;  // packed Delta / Delta-tilde, 4 planes
+  T *G = nullptr;  // g, 9 planes
+  void *tw[4] = {nullptr, nullptr, nullptr, nullptr};
+  std::vector<Pass> passes;
+  FFTTables tables;
+};
+
+}  // namespace
+
+struct lgf_ctx {
+  int n[4];
+  int64_t V;
+  Lattice L;
+  int device = 0;
+  cudaStream_t own_stream = nullptr, stream = nullptr;
+  std::string err;
+  bool poisoned = false;
+  int smem_optin = 0;
+
+  State<double> s64;
+  State<float> s32;
+  double *p2part[4] = {nullptr, nullptr, nullptr, nullptr};
+  double wscale = 0;
+  AxisFFT ax[4];
+
+  double *U0 = nullptr;     // mixed: input links (double planes) for the handover
+  float *Gacc = nullptr;    // mixed/float: accumulated gauge transformation (9 float planes)
+  double *staging = nullptr;  // AoS double buffer for host inputs / outputs and single steps
+  size_t staging_bytes = 0;
+  double *staging2 = nullptr;
+  size_t staging2_bytes = 0;
+  double *partials = nullptr;
+  int nblocks_site = 0;
+  Ctrl *ctrl = nullptr;
+  Ctrl ctrl_host{};
+  double *hist_dev = nullptr;
+  int hist_cap = 0;
+  unsigned int *ran_dev = nullptr;  // per-kernel counts of launches that did work (timing mode)
+
+  // session
+  bool loaded = false;  // a working state is present
+  int load_prec = 0;    // the precision it was loaded with
+  int stage = -1;       // LGF_FP64 or LGF_FP32: precision of the live working links
+  int since_reunit = 0;
+  double prev_theta = 0;  // theta and iteration count at the previous chunk boundary
+  int prev_iters = 0;
+
+  // timing
+  bool timing = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
+  std::vector<int> ev_kid;
+  size_t ev_used = 0;
+  double kms[2 * KID_COUNT] = {0};
+  long klaunch[2 * KID_COUNT] = {0};
+};
+
+namespace {
+
+thread_local std::string g_last_static_error;
+
+lgf_status fail(lgf_ctx *c, lgf_status st, const std::string &msg) {
+  if (c) {
+    c->err = msg;
+    if (st == LGF_ECUDA) c->poisoned = true;
+  } else {
+    g_last_static_error = msg;
+  }
+  return st;
+}
+
+#define CK(call)                                                                                    \
+  do {                                                                                              \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess)                                                                          \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? LGF_ENOMEM : LGF_ECUDA,                    \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                              \
+  } while (0)
+
+#define CKL()                                                                                       \
+  do {                                                                                              \
+    cudaError_t e_ = cudaGetLastError();                                                            \
+    if (e_ != cudaSuccess) return fail(ctx, LGF_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define TRY(x)                   \
+  do {                           \
+    lgf_status s_ = (x);         \
+    if (s_ != LGF_OK) return s_; \
+  } while (0)
+
+bool factor_ok(int n) {
+  if (n < 2 || n > 1024) return false;
+  for (int p : {2, 3, 5})
+    while (n % p == 0) n /= p;
+  return n == 1;
+}
+
+AxisFFT make_axis(int N) {
+  AxisFFT a{};
+  a.N = N;
+  int r = N, k = 0;
+  for (int R : {8, 4, 2, 3, 5})
+    while (r % R == 0 && !(R == 2 && r % 4 == 0)) {
+      a.R[k++] = R;
+      r /= R;
+    }
+  while (r % 2 == 0) {
+    a.R[k++] = 2;
+    r /= 2;
+  }
+  a.nst = k;
+  return a;
+}
+
+// Frequency held at each position after the in-place DIF transform with radices R[0..nst).
+void digit_reversed_freq(const AxisFFT &a, std::vector<int> &kpos) {
+  kpos.assign(a.N, 0);
+  for (int pos = 0; pos < a.N; ++pos) {
+    int N = a.N, p = pos, k = 0, mult = 1;
+    for (int st = 0; st < a.nst; ++st) {
+      const int R = a.R[st];
+      const int M = N / R;
+      const int r = p / M;  // output index r' of this stage
+      k += mult * r;
+      mult *= R;
+      p %= M;
+      N = M;
+    }
+    kpos[pos] = k;
+  }
+}
+
+lgf_status timed_begin(lgf_ctx *ctx, int kid) {
+  if (!ctx->timing) return LGF_OK;
+  if (ctx->ev_used == ctx->ev_pool.size()) {
+    cudaEvent_t a, b;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    ctx->ev_pool.push_back({a, b});
+    ctx->ev_kid.push_back(kid);
+  }
+  ctx->ev_kid[ctx->ev_used] = kid;
+  CK(cudaEventRecord(ctx->ev_pool[ctx->ev_used].first, ctx->stream));
+  return LGF_OK;
+}
+lgf_status timed_end(lgf_ctx *ctx) {
+  if (!ctx->timing) return LGF_OK;
+  CK(cudaEventRecord(ctx->ev_pool[ctx->ev_used].second, ctx->stream));
+  ctx->ev_used++;
+  return LGF_OK;
+}
+lgf_status timed_collect(lgf_ctx *ctx) {
+  for (size_t i = 0; i < ctx->ev_used; ++i) {
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, ctx->ev_pool[i].first, ctx->ev_pool[i].second));
+    ctx->kms[ctx->ev_kid[i]] += ms;
+    ctx->klaunch[ctx->ev_kid[i]] += 1;
+  }
+  ctx->ev_used = 0;
+  return LGF_OK;
+}
+
+template <typename T> lgf_status alloc(lgf_ctx *ctx, T **p, size_t count) {
+  if (*p) return LGF_OK;
+  CK(cudaMalloc((void **)p, count * sizeof(T)));
+  return LGF_OK;
+}
+
+// Plan the FFT passes for element size es (bytes per complex number).
+template <typename T> void plan_passes(lgf_ctx *ctx, State<T> &S) {
+  const int Nx = ctx->n[0], Ny = ctx->n[1], Nz = ctx->n[2], Nt = ctx->n[3];
+  const int64_t Nxy = (int64_t)Nx * Ny, Nxyz = Nxy * Nz;
+  const size_t es = sizeof(cx<T>);
+  const size_t budget = 112 * 1024;  // tile bytes: two blocks per SM
+  const int cmin = (int)std::max<size_t>(1, 64 / es);  // aim for >= 64-byte contiguous runs
+  auto mk = [&](int d0, int d1, int d2, int64_t g0, int64_t g1, int64_t g2, int nb1, int64_t B1, int64_t B2,
+                int nblocks, int nax, int dim0, int mu0, int dim1, int mu1, int mode, int kid) {
+    Pass p{};
+    p.d.d[0] = d0;
+    p.d.d[1] = d1;
+    p.d.d[2] = d2;
+    p.d.g[0] = g0;
+    p.d.g[1] = g1;
+    p.d.g[2] = g2;
+    p.d.nb1 = nb1;
+    p.d.B1 = B1;
+    p.d.B2 = B2;
+    p.d.nblocks = nblocks;
+    p.d.nax = nax;
+    p.d.ax_dim[0] = dim0;
+    p.d.ax_mu[0] = mu0;
+    p.d.ax_dim[1] = dim1;
+    p.d.ax_mu[1] = mu1;
+    p.d.mode = mode;
+    p.kid = kid;
+    const int nel = d0 * d1 * d2;
+    int twn = ctx->n[mu0] + (nax > 1 ? ctx->n[mu1] : 0);
+    p.smem = (size_t)(nel + twn) * es;
+    p.threads = nel >= 2048 ? 512 : 256;
+    return p;
+  };
+  auto largest_run = [&](int64_t extent, int64_t per_col_bytes, int cap) {
+    int best = 1;
+    for (int c = 1; c <= cap && c <= extent; ++c)
+      if (extent % c == 0 && (size_t)(c * per_col_bytes) <= budget) best = c;
+    return best;
+  };
+  std::vector<Pass> fwd, mid, inv;
+  // x and y
+  if ((size_t)Nxy * es <= budget) {
+    const int nb = Nz * Nt;
+    fwd.push_back(mk(Nx, Ny, 1, 1, Nx, 0, nb, Nxy, 0, nb, 2, 0, 0, 1, 1, 0, KID_FFT_XY_FWD));
+    inv.push_back(mk(Nx, Ny, 1, 1, Nx, 0, nb, Nxy, 0, nb, 2, 0, 0, 1, 1, 1, KID_FFT_XY_INV));
+  } else {
+    const int rows = largest_run(Ny * Nz * Nt, (int64_t)Nx * es, 16);
+    const int nbx = (int)(Ny * (int64_t)Nz * Nt / rows);
+    fwd.push_back(mk(Nx, rows, 1, 1, Nx, 0, nbx, (int64_t)rows * Nx, 0, nbx, 1, 0, 0, 0, 0, 0, KID_FFT_X_FWD));
+    const int cy = largest_run(Nx, (int64_t)Ny * es, 64);
+    const int nby = (Nx / cy) * Nz * Nt;
+    fwd.push_back(mk(cy, Ny, 1, 1, Nx, 0, Nx / cy, cy, Nxy, nby, 1, 1, 1, 0, 0, 0, KID_FFT_Y_FWD));
+    inv.push_back(mk(cy, Ny, 1, 1, Nx, 0, Nx / cy, cy, Nxy, nby, 1, 1, 1, 0, 0, 1, KID_FFT_Y_INV));
+    inv.push_back(mk(Nx, rows, 1, 1, Nx, 0, nbx, (int64_t)rows * Nx, 0, nbx, 1, 0, 0, 0, 0, 1, KID_FFT_X_INV));
+  }
+  // z and t, with the filter
+  const int64_t zt_col = (int64_t)Nz * Nt * es;
+  int czt = 0;
+  for (int c = (int)std::min<int64_t>(Nxy, 64); c >= 1; --c)
+    if (Nxy % c == 0 && (size_t)(c * zt_col) <= budget) {
+      czt = c;
+      break;
+    }
+  if (czt >= std::min<int64_t>(cmin, Nxy)) {
+    const int nb = (int)(Nxy / czt);
+    mid.push_back(mk(czt, Nz, Nt, 1, Nxy, Nxyz, nb, czt, 0, nb, 2, 1, 2, 2, 3, 2, KID_FFT_ZT_FILTER));
+  } else {
+    const int cz = largest_run(Nxy, (int64_t)Nz * es, 64);
+    const int nbz = (int)(Nxy / cz) * Nt;
+    fwd.push_back(mk(cz, Nz, 1, 1, Nxy, 0, (int)(Nxy / cz), cz, Nxyz, nbz, 1, 1, 2, 0, 0, 0, KID_FFT_Z_FWD));
+    const int ct = largest_run(Nxyz, (int64_t)Nt * es, 64);
+    const int nbt = (int)(Nxyz / ct);
+    mid.push_back(mk(ct, Nt, 1, 1, Nxyz, 0, nbt, ct, 0, nbt, 1, 1, 3, 0, 0, 2, KID_FFT_T_FILTER));
+    inv.insert(inv.begin(),
+               mk(cz, Nz, 1, 1, Nxy, 0, (int)(Nxy / cz), cz, Nxyz, nbz, 1, 1, 2, 0, 0, 1, KID_FFT_Z_INV));
+  }
+  S.passes.clear();
+  for (auto &p : fwd) S.passes.push_back(p);
+  for (auto &p : mid) S.passes.push_back(p);
+  for (auto &p : inv) S.passes.push_back(p);
+}
+
+template <typename T> lgf_status setup_precision(lgf_ctx *ctx, State<T> &S) {
+  const int64_t V = ctx->V;
+  TRY(alloc(ctx, &S.U, (size_t)4 * 9 * V * 2));
+  TRY(alloc(ctx, &S.P, (size_t)4 * V * 2));
+  TRY(alloc(ctx, &S.G, (size_t)9 * V * 2));
+  if (!S.tw[0]) {
+    for (int mu = 0; mu < 4; ++mu) {
+      const int N = ctx->n[mu];
+      std::vector<T> tw(2 * N);
+      for (int j = 0; j < N; ++j) {
+        // w_N^j = exp(-2 pi i j / N), evaluated in double with the angle reduced to [0, pi/4] by symmetry
+        const long double a = 2.0L * 3.14159265358979323846264338327950288L * (long double)j / (long double)N;
+        tw[2 * j] = (T)std::cos((double)a);
+        tw[2 * j + 1] = (T)(-std::sin((double)a));
+      }
+      CK(cudaMalloc(&S.tw[mu], sizeof(T) * 2 * N));
+      CK(cudaMemcpy(S.tw[mu], tw.data(), sizeof(T) * 2 * N, cudaMemcpyHostToDevice));
+    }
+    plan_passes<T>(ctx, S);
+    for (int mu = 0; mu < 4; ++mu) {
+      S.tables.ax[mu] = ctx->ax[mu];
+      S.tables.tw[mu] = S.tw[mu];
+      S.tables.p2part[mu] = ctx->p2part[mu];
+      S.tables.n[mu] = ctx->n[mu];
+    }
+    S.tables.wscale = ctx->wscale;
+    for (auto &p : S.passes)
+      if (p.smem > 48 * 1024) {
+        CK(cudaFuncSetAttribute(k_fft_pass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::min<size_t>(ctx->smem_optin, 227 * 1024)));
+        break;
+      }
+  }
+  return LGF_OK;
+}
+
+lgf_status ensure_common(lgf_ctx *ctx) {
+  if (!ctx->partials) {
+    ctx->nblocks_site = (int)((ctx->V + NT - 1) / NT);
+    CK(cudaMalloc(&ctx->partials, sizeof(double) * 2 * (size_t)std::max(ctx->nblocks_site, 1)));
+    CK(cudaMalloc(&ctx->ctrl, sizeof(Ctrl)));
+    CK(cudaMemset(ctx->ctrl, 0, sizeof(Ctrl)));
+  }
+  return LGF_OK;
+}
+
+lgf_status ensure_staging(lgf_ctx *ctx, double **buf, size_t *have, size_t bytes) {
+  if (*have >= bytes) return LGF_OK;
+  if (*buf) CK(cudaFree(*buf));
+  *buf = nullptr;
+  *have = 0;
+  CK(cudaMalloc(buf, bytes));
+  *have = bytes;
+  return LGF_OK;
+}
+
+bool is_device_ptr(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Resolve a caller buffer of `bytes` to a device pointer, staging host data through `buf`.
+lgf_status input_ptr(lgf_ctx *ctx, const double *p, size_t bytes, double **buf, size_t *have, const double **out) {
+  if (!p) return fail(ctx, LGF_EINVAL, "null buffer");
+  if (is_device_ptr(p)) {
+    if (((uintptr_t)p) & 15) return fail(ctx, LGF_EINVAL, "device buffers must be 16-byte aligned");
+    *out = p;
+    return LGF_OK;
+  }
+  TRY(ensure_staging(ctx, buf, have, bytes));
+  CK(cudaMemcpyAsync(*buf, p, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  *out = *buf;
+  return LGF_OK;
+}
+
+lgf_status output_ptr(lgf_ctx *ctx, double *p, size_t bytes, double **buf, size_t *have, double **dev, bool *host) {
+  if (!p) return fail(ctx, LGF_EINVAL, "null buffer");
+  if (is_device_ptr(p)) {
+    if (((uintptr_t)p) & 15) return fail(ctx, LGF_EINVAL, "device buffers must be 16-byte aligned");
+    *dev = p;
+    *host = false;
+    return LGF_OK;
+  }
+  TRY(ensure_staging(ctx, buf, have, bytes));
+  *dev = *buf;
+  *host = true;
+  return LGF_OK;
+}
+
+unsigned grid1(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+template <typename T> lgf_status launch_delta(lgf_ctx *ctx, State<T> &S, int counts_update, int check_active) {
+  TRY(timed_begin(ctx, kid<T>(KID_DELTA)));
+  k_delta<T, NT><<<ctx->nblocks_site, NT, 0, ctx->stream>>>(S.U, S.P, ctx->partials, ctx->ctrl, ctx->L,
+                                                            counts_update, check_active, kid<T>(KID_DELTA));
+  CKL();
+  return timed_end(ctx);
+}
+
+template <typename T> lgf_status launch_filter(lgf_ctx *ctx, State<T> &S, T *data, int check_active) {
+  for (auto &p : S.passes) {
+    TRY(timed_begin(ctx, kid<T>(p.kid)));
+    dim3 grid(p.d.nblocks, 4);
+    k_fft_pass<T><<<grid, p.threads, p.smem, ctx->stream>>>(data, ctx->V, p.d, S.tables, ctx->ctrl, check_active,
+                                                             kid<T>(p.kid));
+    CKL();
+    TRY(timed_end(ctx));
+  }
+  return LGF_OK;
+}
+
+template <typename T> lgf_status launch_gauge(lgf_ctx *ctx, State<T> &S, double alpha, int check_active) {
+  TRY(timed_begin(ctx, kid<T>(KID_GAUGE)));
+  k_gauge<T, NT><<<grid1(ctx->V, NT), NT, 0, ctx->stream>>>(S.P, S.G, (T)(0.5 * alpha), ctx->V, ctx->ctrl,
+                                                            check_active, kid<T>(KID_GAUGE));
+  CKL();
+  return timed_end(ctx);
+}
+
+template <typename T> lgf_status launch_update(lgf_ctx *ctx, State<T> &S, int check_active) {
+  TRY(timed_begin(ctx, kid<T>(KID_UPDATE)));
+  k_update<T, NT><<<grid1(ctx->V, NT), NT, 0, ctx->stream>>>(S.U, S.G, ctx->L, ctx->ctrl, check_active,
+                                                             kid<T>(KID_UPDATE));
+  CKL();
+  return timed_end(ctx);
+}
+
+// One iteration of the loop of Algorithm 1 on state S (kernels return at once once the loop stops).
+template <typename T> lgf_status launch_iteration(lgf_ctx *ctx, State<T> &S, double alpha, bool accumulate) {
+  TRY(launch_filter<T>(ctx, S, S.P, 1));
+  TRY(launch_gauge<T>(ctx, S, alpha, 1));
+  if (accumulate) {
+    TRY(timed_begin(ctx, kid<float>(KID_UPDATE_ACC)));
+    k_update_accumulate<NT><<<grid1(ctx->V, NT), NT, 0, ctx->stream>>>(ctx->s32.U, ctx->s32.G, ctx->Gacc, ctx->L,
+                                                                        ctx->ctrl, kid<float>(KID_UPDATE_ACC));
+    CKL();
+    TRY(timed_end(ctx));
+  } else {
+    TRY(launch_update<T>(ctx, S, 1));
+  }
+  return launch_delta<T>(ctx, S, 1, 1);
+}
+
+lgf_status read_ctrl(lgf_ctx *ctx) {
+  CK(cudaMemcpyAsync(&ctx->ctrl_host, ctx->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (ctx->timing) TRY(timed_collect(ctx));
+  return LGF_OK;
+}
+
+lgf_status write_ctrl(lgf_ctx *ctx) {
+  ctx->ctrl_host.ran = ctx->timing ? ctx->ran_dev : nullptr;
+  CK(cudaMemcpyAsync(ctx->ctrl, &ctx->ctrl_host, sizeof(Ctrl), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return LGF_OK;
+}
+
+// Reproject the float links and the accumulated transformation onto SU(3) in double precision.
+lgf_status launch_reunit(lgf_ctx *ctx) {
+  TRY(timed_begin(ctx, kid<float>(KID_REUNIT)));
+  k_reunitarize_fp64<NT><<<grid1(ctx->V * 5, NT), NT, 0, ctx->stream>>>(ctx->s32.U, ctx->Gacc, ctx->V, ctx->ctrl,
+                                                                       kid<float>(KID_REUNIT));
+  CKL();
+  return timed_end(ctx);
+}
+
+// Mixed handover: G from the float accumulation (reprojected in double), then
+// U = G U0 G^+(x+mu) in double precision from the saved input (exact gauge equivalence).
+lgf_status handover(lgf_ctx *ctx) {
+  TRY(setup_precision<double>(ctx, ctx->s64));
+  TRY(timed_begin(ctx, kid<double>(KID_GACC_TO_DOUBLE)));
+  k_gacc_to_double<NT><<<grid1(ctx->V, NT), NT, 0, ctx->stream>>>(ctx->Gacc, ctx->s64.G, ctx->V);
+  CKL();
+  TRY(timed_end(ctx));
+  TRY(timed_begin(ctx, kid<double>(KID_TRANSFORM_FROM)));
+  k_transform_from<NT><<<grid1(ctx->V, NT), NT, 0, ctx->stream>>>(ctx->U0, ctx->s64.U, ctx->s64.G, ctx->L);
+  CKL();
+  return timed_end(ctx);
+}
+
+// Timed wrappers of the layout conversions used by load and store.
+template <typename T> lgf_status to_planes(lgf_ctx *ctx, const double *src, T *dst, int nmat) {
+  TRY(timed_begin(ctx, kid<T>(KID_TO_PLANES)));
+  k_aos_to_planes<T><<<grid1((int64_t)nmat * ctx->V, NT), NT, 0, ctx->stream>>>(src, dst, ctx->V, nmat);
+  CKL();
+  return timed_end(ctx);
+}
+template <typename T> lgf_status from_planes(lgf_ctx *ctx, const T *src, double *dst, int nmat) {
+  TRY(timed_begin(ctx, kid<T>(KID_FROM_PLANES)));
+  k_planes_to_aos<T><<<grid1((int64_t)nmat * ctx->V, NT), NT, 0, ctx->stream>>>(src, dst, ctx->V, nmat);
+  CKL();
+  return timed_end(ctx);
+}
+
+lgf_status upload_hist(lgf_ctx *ctx, const lgf_options *opt) {
+  ctx->ctrl_host.hist = nullptr;
+  ctx->ctrl_host.hist_len = 0;
+  if (opt && opt->history && opt->history_len > 0) {
+    if (opt->history_len > ctx->hist_cap) {
+      if (ctx->hist_dev) CK(cudaFree(ctx->hist_dev));
+      ctx->hist_dev = nullptr;
+      CK(cudaMalloc(&ctx->hist_dev, sizeof(double) * 2 * opt->history_len));
+      ctx->hist_cap = opt->history_len;
+    }
+    CK(cudaMemsetAsync(ctx->hist_dev, 0, sizeof(double) * 2 * opt->history_len, ctx->stream));
+    ctx->ctrl_host.hist = ctx->hist_dev;
+    ctx->ctrl_host.hist_len = opt->history_len;
+  }
+  return LGF_OK;
+}
+
+lgf_status check_ctx(lgf_ctx *ctx) {
+  if (!ctx) return fail(nullptr, LGF_EINVAL, "null context");
+  if (ctx->poisoned) return LGF_ECUDA;
+  CK(cudaSetDevice(ctx->device));
+  return LGF_OK;
+}
+
+}  // namespace
+
+// ============================================== C ABI ===============================================
+extern "C" {
+
+void lgf_default_options(lgf_options *opt) {
+  if (!opt) return;
+  opt->precision = LGF_FP64;
+  opt->theta_switch = 1e-8;
+  opt->reunit_period = 16;
+  opt->max_iter = 100000;
+  opt->history = nullptr;
+  opt->history_len = 0;
+}
+
+lgf_status lgf_create(int Nx, int Ny, int Nz, int Nt, lgf_ctx **out) {
+  if (!out) return fail(nullptr, LGF_EINVAL, "null output pointer");
+  *out = nullptr;
+  const int n[4] = {Nx, Ny, Nz, Nt};
+  for (int mu = 0; mu < 4; ++mu)
+    if (!factor_ok(n[mu]))
+      return fail(nullptr, LGF_EINVAL, "lattice extents must be in [2, 1024] and products of 2, 3 and 5");
+  lgf_ctx *ctx = new lgf_ctx();
+  for (int mu = 0; mu < 4; ++mu) ctx->n[mu] = n[mu];
+  ctx->V = (int64_t)Nx * Ny * Nz * Nt;
+  ctx->L.V = ctx->V;
+  int64_t st = 1;
+  for (int mu = 0; mu < 4; ++mu) {
+    ctx->L.n[mu] = n[mu];
+    ctx->L.stride[mu] = st;
+    st *= n[mu];
+  }
+  auto bail = [&](lgf_status s, const std::string &m) {
+    g_last_static_error = m;
+    delete ctx;
+    return s;
+  };
+  if (cudaGetDevice(&ctx->device) != cudaSuccess) return bail(LGF_ECUDA, "no CUDA device");
+  if (cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return bail(LGF_ECUDA, "cudaStreamCreate failed");
+  ctx->stream = ctx->own_stream;
+  cudaDeviceGetAttribute(&ctx->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+  // p^2 tables (position -> 4 sin^2(pi k / N)) and the filter scale p^2_max / V
+  double p2max = 0;
+  for (int mu = 0; mu < 4; ++mu) {
+    ctx->ax[mu] = make_axis(n[mu]);
+    std::vector<int> kpos;
+    digit_reversed_freq(ctx->ax[mu], kpos);
+    std::vector<double> part(n[mu]);
+    for (int p = 0; p < n[mu]; ++p) {
+      const double sn = std::sin(M_PI * (double)kpos[p] / (double)n[mu]);
+      part[p] = 4.0 * sn * sn;
+    }
+    const double sm = std::sin(M_PI * (double)(n[mu] / 2) / (double)n[mu]);
+    p2max += 4.0 * sm * sm;
+    if (cudaMalloc(&ctx->p2part[mu], sizeof(double) * n[mu]) != cudaSuccess ||
+        cudaMemcpy(ctx->p2part[mu], part.data(), sizeof(double) * n[mu], cudaMemcpyHostToDevice) != cudaSuccess) {
+      lgf_destroy(ctx);
+      g_last_static_error = "allocation of FFT tables failed";
+      return LGF_ENOMEM;
+    }
+  }
+  ctx->wscale = p2max / (double)ctx->V;
+  *out = ctx;
+  return LGF_OK;
+}
+
+void lgf_destroy(lgf_ctx *ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  auto fr = [](void *p) {
+    if (p) cudaFree(p);
+  };
+  fr(ctx->s64.U);
+  fr(ctx->s64.P);
+  fr(ctx->s64.G);
+  fr(ctx->s32.U);
+  fr(ctx->s32.P);
+  fr(ctx->s32.G);
+  for (int mu = 0; mu < 4; ++mu) {
+    fr(ctx->s64.tw[mu]);
+    fr(ctx->s32.tw[mu]);
+    fr(ctx->p2part[mu]);
+  }
+  fr(ctx->U0);
+  fr(ctx->Gacc);
+  fr(ctx->staging);
+  fr(ctx->staging2);
+  fr(ctx->partials);
+  fr(ctx->ctrl);
+  fr(ctx->hist_dev);
+  fr(ctx->ran_dev);
+  for (auto &e : ctx->ev_pool) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
+  if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+  delete ctx;
+}
+
+const char *lgf_last_error(const lgf_ctx *ctx) {
+  if (!ctx) return g_last_static_error.c_str();
+  return ctx->err.c_str();
+}
+
+lgf_status lgf_set_stream(lgf_ctx *ctx, void *stream) {
+  TRY(check_ctx(ctx));
+  ctx->stream = stream ? (cudaStream_t)stream : ctx->own_stream;
+  return LGF_OK;
+}
+
+lgf_status lgf_load(lgf_ctx *ctx, const double *links, int precision) {
+  TRY(check_ctx(ctx));
+  if (precision != LGF_FP64 && precision != LGF_MIXED && precision != LGF_FP32)
+    return fail(ctx, LGF_EINVAL, "unknown precision");
+  TRY(ensure_common(ctx));
+  const int64_t V = ctx->V;
+  const size_t bytes = (size_t)4 * V * 9 * 16;
+  const double *src = nullptr;
+  TRY(input_ptr(ctx, links, bytes, &ctx->staging, &ctx->staging_bytes, &src));
+  memset(&ctx->ctrl_host, 0, sizeof(Ctrl));
+  ctx->ctrl_host.active = 1;
+  ctx->ctrl_host.limit = 0;
+  ctx->ctrl_host.threshold = 0;
+  TRY(write_ctrl(ctx));
+  if (precision == LGF_FP64) {
+    TRY(setup_precision<double>(ctx, ctx->s64));
+    TRY(to_planes<double>(ctx, src, ctx->s64.U, 4));
+    TRY(launch_delta<double>(ctx, ctx->s64, 0, 0));
+    ctx->stage = LGF_FP64;
+  } else {
+    TRY(setup_precision<float>(ctx, ctx->s32));
+    TRY(alloc(ctx, &ctx->Gacc, (size_t)9 * V * 2));
+    if (precision == LGF_MIXED) {
+      TRY(alloc(ctx, &ctx->U0, (size_t)4 * 9 * V * 2));
+      TRY(to_planes<double>(ctx, src, ctx->U0, 4));
+    }
+    TRY(to_planes<float>(ctx, src, ctx->s32.U, 4));
+    TRY(timed_begin(ctx, kid<float>(KID_SET_IDENTITY)));
+    k_set_identity<<<grid1(V, NT), NT, 0, ctx->stream>>>(ctx->Gacc, V);
+    CKL();
+    TRY(timed_end(ctx));
+    TRY(launch_delta<float>(ctx, ctx->s32, 0, 0));
+    ctx->stage = LGF_FP32;
+  }
+  TRY(read_ctrl(ctx));
+  ctx->loaded = true;
+  ctx->load_prec = precision;
+  ctx->since_reunit = 0;
+  ctx->prev_theta = 0;
+  ctx->prev_iters = 0;
+  return LGF_OK;
+}
+
+lgf_status lgf_iterate(lgf_ctx *ctx, int max_new, double alpha, double eps, const lgf_options *opt, double *theta,
+                       double *F, int *iters) {
+  TRY(check_ctx(ctx));
+  if (!ctx->loaded) return fail(ctx, LGF_EINVAL, "lgf_iterate before lgf_load");
+  if (max_new < 0 || !(alpha > 0) || !(eps >= 0)) return fail(ctx, LGF_EINVAL, "bad max_new, alpha or eps");
+  lgf_options o;
+  lgf_default_options(&o);
+  if (opt) o = *opt;
+  if (o.reunit_period < 1) o.reunit_period = 1;
+  TRY(upload_hist(ctx, opt));
+  if (ctx->ctrl_host.hist && ctx->ctrl_host.iters < ctx->ctrl_host.hist_len) {
+    // record the state the call starts from
+    double h[2] = {ctx->ctrl_host.theta, ctx->ctrl_host.F};
+    CK(cudaMemcpyAsync(ctx->ctrl_host.hist + 2 * ctx->ctrl_host.iters, h, sizeof h, cudaMemcpyHostToDevice,
+                       ctx->stream));
+  }
+  const int target = ctx->ctrl_host.iters + max_new;
+  lgf_status result = LGF_ENOCONV;
+  for (;;) {
+    const bool float_stage = ctx->stage == LGF_FP32;
+    const bool mixed_float = float_stage && ctx->load_prec == LGF_MIXED;
+    const double thr = mixed_float ? std::max(eps, o.theta_switch) : eps;
+    Ctrl &c = ctx->ctrl_host;
+    if (c.status == 5) {
+      result = LGF_ENONFINITE;
+      break;
+    }
+    if (c.theta < thr || c.iters >= target) {
+      if (mixed_float && c.theta < thr) {
+        // hand over to double precision: rebuild the links from the input and G, then Delta, theta, F
+        TRY(handover(ctx));
+        ctx->stage = LGF_FP64;
+        c.active = 1;
+        TRY(write_ctrl(ctx));
+        TRY(launch_delta<double>(ctx, ctx->s64, 0, 0));
+        TRY(read_ctrl(ctx));
+        continue;
+      }
+      result = (c.theta < eps) ? LGF_OK : LGF_ENOCONV;
+      break;
+    }
+    c.threshold = thr;
+    c.limit = target;
+    c.active = 1;
+    TRY(write_ctrl(ctx));
+    // a chunk of iterations without host round trips; kernels return at once after the loop stops.
+    // The chunk is sized from the observed geometric convergence rate so that few launches are idle.
+    int chunk = 8;
+    if (ctx->prev_theta > 0 && c.theta > 0 && c.theta < ctx->prev_theta && ctx->prev_iters < c.iters) {
+      const double rate = std::pow(c.theta / ctx->prev_theta, 1.0 / (c.iters - ctx->prev_iters));
+      const double need = std::ceil(std::log(thr / c.theta) / std::log(rate));
+      if (need >= 1 && need < chunk) chunk = (int)need;
+    }
+    ctx->prev_theta = c.theta;
+    ctx->prev_iters = c.iters;
+    for (int k = 0; k < chunk; ++k) {
+      if (float_stage) {
+        TRY(launch_iteration<float>(ctx, ctx->s32, alpha, true));
+        if (++ctx->since_reunit >= o.reunit_period) {
+          TRY(launch_reunit(ctx));
+          ctx->since_reunit = 0;
+        }
+      } else {
+        TRY(launch_iteration<double>(ctx, ctx->s64, alpha, false));
+      }
+    }
+    TRY(read_ctrl(ctx));
+  }
+  if (theta) *theta = ctx->ctrl_host.theta;
+  if (F) *F = ctx->ctrl_host.F;
+  if (iters) *iters = ctx->ctrl_host.iters;
+  if (opt && opt->history && opt->history_len > 0) {
+    CK(cudaMemcpyAsync(opt->history, ctx->hist_dev, sizeof(double) * 2 * opt->history_len, cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  if (result == LGF_ENONFINITE) return fail(ctx, LGF_ENONFINITE, "theta or F is not finite");
+  return result;
+}
+
+lgf_status lgf_store(lgf_ctx *ctx, double *links) {
+  TRY(check_ctx(ctx));
+  if (!ctx->loaded) return fail(ctx, LGF_EINVAL, "lgf_store before lgf_load");
+  const int64_t V = ctx->V;
+  const size_t bytes = (size_t)4 * V * 9 * 16;
+  double *dst = nullptr;
+  bool host = false;
+  TRY(output_ptr(ctx, links, bytes, &ctx->staging, &ctx->staging_bytes, &dst, &host));
+  if (ctx->stage == LGF_FP64) {
+    TRY(from_planes<double>(ctx, ctx->s64.U, dst, 4));
+  } else if (ctx->load_prec == LGF_MIXED) {
+    TRY(handover(ctx));
+    TRY(from_planes<double>(ctx, ctx->s64.U, dst, 4));
+  } else {
+    TRY(from_planes<float>(ctx, ctx->s32.U, dst, 4));
+  }
+  if (host) CK(cudaMemcpyAsync(links, dst, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return LGF_OK;
+}
+
+lgf_status lgf_fix(lgf_ctx *ctx, double *links, double alpha, double eps, const lgf_options *opt, double *theta_out,
+                   double *F_out, int *iters_out) {
+  lgf_options o;
+  lgf_default_options(&o);
+  if (opt) o = *opt;
+  TRY(lgf_load(ctx, links, o.precision));
+  double th = 0, F = 0;
+  int it = 0;
+  lgf_status st = lgf_iterate(ctx, o.max_iter, alpha, eps, &o, &th, &F, &it);
+  if (st != LGF_OK && st != LGF_ENOCONV) return st;
+  TRY(lgf_store(ctx, links));
+  if (theta_out) *theta_out = th;
+  if (F_out) *F_out = F;
+  if (iters_out) *iters_out = it;
+  return st;
+}
+
+lgf_status lgf_measure(lgf_ctx *ctx, const double *links, double *theta, double *F, double *plaq) {
+  TRY(check_ctx(ctx));
+  TRY(ensure_common(ctx));
+  TRY(setup_precision<double>(ctx, ctx->s64));
+  const int64_t V = ctx->V;
+  const double *src = nullptr;
+  TRY(input_ptr(ctx, links, (size_t)4 * V * 9 * 16, &ctx->staging, &ctx->staging_bytes, &src));
+  k_aos_to_planes<double><<<grid1(4 * V, NT), NT, 0, ctx->stream>>>(src, ctx->s64.U, V, 4);
+  CKL();
+  memset(&ctx->ctrl_host, 0, sizeof(Ctrl));
+  TRY(write_ctrl(ctx));
+  TRY(launch_delta<double>(ctx, ctx->s64, 0, 0));
+  TRY(read_ctrl(ctx));
+  if (theta) *theta = ctx->ctrl_host.theta;
+  if (F) *F = ctx->ctrl_host.F;
+  if (plaq) {
+    k_plaquette<double, NT><<<ctx->nblocks_site, NT, 0, ctx->stream>>>(ctx->s64.U, ctx->partials, ctx->L);
+    CKL();
+    std::vector<double> part(ctx->nblocks_site);
+    CK(cudaMemcpyAsync(part.data(), ctx->partials, sizeof(double) * ctx->nblocks_site, cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    double s = 0;
+    for (double v : part) s += v;
+    *plaq = s / (3.0 * 6.0 * (double)V);
+  }
+  ctx->loaded = false;  // the working links were overwritten
+  return LGF_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------- single steps ----------------------------------
+template <typename T> static lgf_status step_delta(lgf_ctx *ctx, State<T> &S, const double *src, double *dst,
+                                                   double *theta, double *F) {
+  const int64_t V = ctx->V;
+  k_aos_to_planes<T><<<grid1(4 * V, NT), NT, 0, ctx->stream>>>(src, S.U, V, 4);
+  CKL();
+  memset(&ctx->ctrl_host, 0, sizeof(Ctrl));
+  TRY(write_ctrl(ctx));
+  TRY(launch_delta<T>(ctx, S, 0, 0));
+  k_unpack_antiherm<T><<<grid1(V, NT), NT, 0, ctx->stream>>>(S.P, dst, V);
+  CKL();
+  TRY(read_ctrl(ctx));
+  if (theta) *theta = ctx->ctrl_host.theta;
+  if (F) *F = ctx->ctrl_host.F;
+  return LGF_OK;
+}
+
+extern "C" lgf_status lgf_delta(lgf_ctx *ctx, const double *links, double *delta, double *theta, double *F, int precision) {
+  TRY(check_ctx(ctx));
+  TRY(ensure_common(ctx));
+  const int64_t V = ctx->V;
+  const double *src = nullptr;
+  TRY(input_ptr(ctx, links, (size_t)4 * V * 144, &ctx->staging, &ctx->staging_bytes, &src));
+  double *dst = nullptr;
+  bool host = false;
+  TRY(output_ptr(ctx, delta, (size_t)V * 144, &ctx->staging2, &ctx->staging2_bytes, &dst, &host));
+  if (precision == LGF_FP32) {
+    TRY(setup_precision<float>(ctx, ctx->s32));
+    TRY(step_delta<float>(ctx, ctx->s32, src, dst, theta, F));
+  } else {
+    TRY(setup_precision<double>(ctx, ctx->s64));
+    TRY(step_delta<double>(ctx, ctx->s64, src, dst, theta, F));
+  }
+  if (host) CK(cudaMemcpyAsync(delta, dst, (size_t)V * 144, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->loaded = false;
+  return LGF_OK;
+}
+
+template <typename T> static lgf_status step_filter(lgf_ctx *ctx, State<T> &S, const double *src, double *dst) {
+  const int64_t V = ctx->V;
+  k_pack_antiherm<T><<<grid1(V, NT), NT, 0, ctx->stream>>>(src, S.P, V);
+  CKL();
+  TRY(launch_filter<T>(ctx, S, S.P, 0));
+  k_unpack_antiherm<T><<<grid1(V, NT), NT, 0, ctx->stream>>>(S.P, dst, V);
+  CKL();
+  return LGF_OK;
+}
+
+extern "C" lgf_status lgf_filter(lgf_ctx *ctx, const double *delta, double *dtilde, int precision) {
+  TRY(check_ctx(ctx));
+  TRY(ensure_common(ctx));
+  const int64_t V = ctx->V;
+  const double *src = nullptr;
+  TRY(input_ptr(ctx, delta, (size_t)V * 144, &ctx->staging, &ctx->staging_bytes, &src));
+  double *dst = nullptr;
+  bool host = false;
+  TRY(output_ptr(ctx, dtilde, (size_t)V * 144, &ctx->staging2, &ctx->staging2_bytes, &dst, &host));
+  if (precision == LGF_FP32) {
+    TRY(setup_precision<float>(ctx, ctx->s32));
+    TRY(step_filter<float>(ctx, ctx->s32, src, dst));
+  } else {
+    TRY(setup_precision<double>(ctx, ctx->s64));
+    TRY(step_filter<double>(ctx, ctx->s64, src, dst));
+  }
+  if (host) CK(cudaMemcpyAsync(dtilde, dst, (size_t)V * 144, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->loaded = false;
+  return LGF_OK;
+}
+
+template <typename T> static lgf_status step_gauge(lgf_ctx *ctx, State<T> &S, const double *src, double alpha,
+                                                   double *dst) {
+  const int64_t V = ctx->V;
+  k_pack_antiherm<T><<<grid1(V, NT), NT, 0, ctx->stream>>>(src, S.P, V);
+  CKL();
+  TRY(launch_gauge<T>(ctx, S, alpha, 0));
+  k_planes_to_aos<T><<<grid1(V, NT), NT, 0, ctx->stream>>>(S.G, dst, V, 1);
+  CKL();
+  return LGF_OK;
+}
+
+extern "C" lgf_status lgf_gauge(lgf_ctx *ctx, const double *dtilde, double alpha, double *g, int precision) {
+  TRY(check_ctx(ctx));
+  TRY(ensure_common(ctx));
+  const int64_t V = ctx->V;
+  const double *src = nullptr;
+  TRY(input_ptr(ctx, dtilde, (size_t)V * 144, &ctx->staging, &ctx->staging_bytes, &src));
+  double *dst = nullptr;
+  bool host = false;
+  TRY(output_ptr(ctx, g, (size_t)V * 144, &ctx->staging2, &ctx->staging2_bytes, &dst, &host));
+  if (precision == LGF_FP32) {
+    TRY(setup_precision<float>(ctx, ctx->s32));
+    TRY(step_gauge<float>(ctx, ctx->s32, src, alpha, dst));
+  } else {
+    TRY(setup_precision<double>(ctx, ctx->s64));
+    TRY(step_gauge<double>(ctx, ctx->s64, src, alpha, dst));
+  }
+  if (host) CK(cudaMemcpyAsync(g, dst, (size_t)V * 144, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->loaded = false;
+  return LGF_OK;
+}
+
+template <typename T> static lgf_status step_update(lgf_ctx *ctx, State<T> &S, const double *lsrc, const double *gsrc,
+                                                    double *dst) {
+  const int64_t V = ctx->V;
+  k_aos_to_planes<T><<<grid1(4 * V, NT), NT, 0, ctx->stream>>>(lsrc, S.U, V, 4);
+  CKL();
+  k_aos_to_planes<T><<<grid1(V, NT), NT, 0, ctx->stream>>>(gsrc, S.G, V, 1);
+  CKL();
+  TRY(launch_update<T>(ctx, S, 0));
+  k_planes_to_aos<T><<<grid1(4 * V, NT), NT, 0, ctx->stream>>>(S.U, dst, V, 4);
+  CKL();
+  return LGF_OK;
+}
+
+extern "C" lgf_status lgf_update(lgf_ctx *ctx, double *links, const double *g, int precision) {
+  TRY(check_ctx(ctx));
+  TRY(ensure_common(ctx));
+  const int64_t V = ctx->V;
+  double *ldev = nullptr;
+  bool host = false;
+  TRY(output_ptr(ctx, links, (size_t)4 * V * 144, &ctx->staging, &ctx->staging_bytes, &ldev, &host));
+  if (host) CK(cudaMemcpyAsync(ldev, links, (size_t)4 * V * 144, cudaMemcpyHostToDevice, ctx->stream));
+  const double *gdev = nullptr;
+  TRY(input_ptr(ctx, g, (size_t)V * 144, &ctx->staging2, &ctx->staging2_bytes, &gdev));
+  if (precision == LGF_FP32) {
+    TRY(setup_precision<float>(ctx, ctx->s32));
+    TRY(step_update<float>(ctx, ctx->s32, ldev, gdev, ldev));
+  } else {
+    TRY(setup_precision<double>(ctx, ctx->s64));
+    TRY(step_update<double>(ctx, ctx->s64, ldev, gdev, ldev));
+  }
+  if (host) CK(cudaMemcpyAsync(links, ldev, (size_t)4 * V * 144, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->loaded = false;
+  return LGF_OK;
+}
+
+extern "C" {
+
+lgf_status lgf_enable_timing(lgf_ctx *ctx, int enable) {
+  TRY(check_ctx(ctx));
+  if (enable && !ctx->ran_dev) {
+    CK(cudaMalloc(&ctx->ran_dev, sizeof(unsigned int) * 2 * KID_COUNT));
+    CK(cudaMemset(ctx->ran_dev, 0, sizeof(unsigned int) * 2 * KID_COUNT));
+  }
+  ctx->timing = enable != 0;
+  return LGF_OK;
+}
+
+lgf_status lgf_kernel_times(lgf_ctx *ctx, const char **name, long *launches, double *ms, int cap, int *count) {
+  TRY(check_ctx(ctx));
+  CK(cudaStreamSynchronize(ctx->stream));
+  TRY(timed_collect(ctx));
+  if (ctx->ran_dev) {
+    // kernels of the loop return at once after the loop has stopped: report the launches that ran
+    unsigned int ran[2 * KID_COUNT];
+    CK(cudaMemcpy(ran, ctx->ran_dev, sizeof ran, cudaMemcpyDeviceToHost));
+    CK(cudaMemset(ctx->ran_dev, 0, sizeof ran));
+    const int loop_kids[] = {KID_DELTA, KID_FFT_XY_FWD, KID_FFT_X_FWD, KID_FFT_Y_FWD, KID_FFT_Z_FWD,
+                             KID_FFT_ZT_FILTER, KID_FFT_T_FILTER, KID_FFT_Z_INV, KID_FFT_Y_INV, KID_FFT_X_INV,
+                             KID_FFT_XY_INV, KID_GAUGE, KID_UPDATE, KID_UPDATE_ACC, KID_REUNIT};
+    for (int k : loop_kids)
+      for (int h = 0; h < 2; ++h) {
+        const int i = k + h * KID_COUNT;
+        if (ctx->klaunch[i] > 0) ctx->klaunch[i] = ran[i];
+        if (ctx->klaunch[i] == 0) ctx->kms[i] = 0;
+      }
+  }
+  int k = 0;
+  if (kKernelNames[0].empty())
+    for (int i = 0; i < 2 * KID_COUNT; ++i)
+      kKernelNames[i] = std::string(kKernelBase[i % KID_COUNT]) + (i < KID_COUNT ? ".f64" : ".f32");
+  for (int i = 0; i < 2 * KID_COUNT; ++i)
+    if (ctx->klaunch[i] > 0) {
+      if (k < cap) {
+        if (name) name[k] = kKernelNames[i].c_str();
+        if (launches) launches[k] = ctx->klaunch[i];
+        if (ms) ms[k] = ctx->kms[i];
+      }
+      ++k;
+      ctx->klaunch[i] = 0;
+      ctx->kms[i] = 0;
+    }
+  if (count) *count = k;
+  return LGF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,330 @@
+// site_kernels.cuh -- per-site kernels of one iteration of Algorithm 1 (Landau gauge fixing with
+// Fourier acceleration): the Delta stencil with the theta/F reductions (Eqs. 1, 3-5), the formation
+// of g (Eq. 2 to first order, then projection to SU(3)) and the gauge update of the links.
+//
+// Working layout (structure of arrays, one plane of V complex numbers per matrix element):
+//   links  U[(mu*9 + e)*V + s]   mu = 0..3, e = 3*row + col
+//   g      G[e*V + s]
+//   packed Delta (and Delta-tilde) P[f*V + s], f = 0..3:
+//     P0 = Delta_01, P1 = Delta_02, P2 = Delta_12, P3 = Im Delta_00 + i Im Delta_11.
+//   Delta is anti-Hermitian and traceless, so these 8 reals determine it; the Fourier filter is real
+//   and even in k, so it maps each packed field onto the packed field of the filtered matrix.
+#pragma once
+#include "su3.cuh"
+
+namespace lgf {
+
+struct Lattice {
+  int n[4];         // Nx, Ny, Nz, Nt
+  int64_t V;
+  int64_t stride[4];  // 1, Nx, Nx*Ny, Nx*Ny*Nz
+};
+
+// Loop control shared by the kernels of the iteration, kept in device memory so that a sequence of
+// iterations runs without host round trips.
+struct Ctrl {
+  double theta, F;       // values after the latest Delta evaluation
+  double threshold;      // iterate while theta >= threshold
+  int iters;             // gauge updates applied since load
+  int limit;             // stop when iters reaches this
+  int active;            // 1 while the loop runs; kernels return at once when 0
+  int status;            // 0 ok, 5 non-finite theta or F
+  unsigned int ticket;   // last-block counter of the reduction
+  int hist_len;
+  double *hist;          // device history: hist[2k], hist[2k+1] = theta, F after k updates
+  unsigned int *ran;     // optional per-kernel counters of launches that did work (timing mode)
+};
+
+// Count a launch that does work (block 0, thread 0), for the per-kernel timing statistics.
+__device__ __forceinline__ void count_run(const Ctrl *ctrl, int tkid) {
+  if (ctrl->ran && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) atomicAdd(ctrl->ran + tkid, 1u);
+}
+
+__device__ __forceinline__ int64_t site_back(const Lattice &L, int64_t s, int mu, int c) {
+  return c == 0 ? s + (int64_t)(L.n[mu] - 1) * L.stride[mu] : s - L.stride[mu];
+}
+__device__ __forceinline__ int64_t site_fwd(const Lattice &L, int64_t s, int mu, int c) {
+  return c == L.n[mu] - 1 ? s - (int64_t)(L.n[mu] - 1) * L.stride[mu] : s + L.stride[mu];
+}
+__device__ __forceinline__ void site_coords(const Lattice &L, int64_t s, int c[4]) {
+  int64_t r = s;
+  c[0] = (int)(r % L.n[0]);
+  r /= L.n[0];
+  c[1] = (int)(r % L.n[1]);
+  r /= L.n[1];
+  c[2] = (int)(r % L.n[2]);
+  c[3] = (int)(r / L.n[2]);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum a and b over the block (deterministic order); the result is valid in thread 0.
+template <int NT> __device__ __forceinline__ void block_sum2(double &a, double &b) {
+  __shared__ double sa[NT / 32], sb[NT / 32];
+  a = warp_sum(a);
+  b = warp_sum(b);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    sa[w] = a;
+    sb[w] = b;
+  }
+  __syncthreads();
+  if (w == 0) {
+    a = l < NT / 32 ? sa[l] : 0.0;
+    b = l < NT / 32 ? sb[l] : 0.0;
+    a = warp_sum(a);
+    b = warp_sum(b);
+  }
+}
+
+// Writes this block's (sum_theta, sum_F) partial; the last block to arrive reduces all partials in a
+// fixed order and updates the loop control (Algorithm 1: "calculate Delta(x), F and theta", then the
+// while-test theta >= eps).
+template <int NT>
+__device__ __forceinline__ void reduce_and_finalize(double th, double f, double *partials, Ctrl *ctrl, int64_t V,
+                                                    int counts_update) {
+  __shared__ bool last;
+  block_sum2<NT>(th, f);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = th;
+    partials[2 * blockIdx.x + 1] = f;
+    __threadfence();
+    const unsigned nb = gridDim.x;
+    last = (atomicAdd(&ctrl->ticket, 1u) == nb - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double a = 0.0, b = 0.0;
+  for (unsigned k = threadIdx.x; k < gridDim.x; k += NT) {
+    a += __ldcg(partials + 2 * k);
+    b += __ldcg(partials + 2 * k + 1);
+  }
+  __syncthreads();
+  block_sum2<NT>(a, b);
+  if (threadIdx.x == 0) {
+    const double theta = a / (3.0 * (double)V);  // Eq. 4: 1/(N_c V) sum_x Tr[Delta Delta^+]
+    const double F = b / (12.0 * (double)V);     // Eq. 1 at g = 1: 1/(4 N_c V) sum Re Tr U
+    ctrl->ticket = 0;
+    int it = ctrl->iters + counts_update;
+    ctrl->iters = it;
+    ctrl->theta = theta;
+    ctrl->F = F;
+    if (ctrl->hist && it < ctrl->hist_len) {
+      ctrl->hist[2 * it] = theta;
+      ctrl->hist[2 * it + 1] = F;
+    }
+    if (!isfinite(theta) || !isfinite(F)) {
+      ctrl->status = 5;
+      ctrl->active = 0;
+    } else {
+      ctrl->active = (theta >= ctrl->threshold) && (it < ctrl->limit);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// a1/a2: Delta(x) = sum_nu [U_nu(x-nu) - U_nu(x) - h.c. - trace] (Eqs. 3, 5), theta and F partials.
+// One thread per site; each loads its 4 links and the 4 backward-neighbour links.
+// ---------------------------------------------------------------------------------------------
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_delta(const T *__restrict__ U, T *__restrict__ P, double *partials, Ctrl *ctrl,
+                                             Lattice L, int counts_update, int check_active, int tkid) {
+  if (check_active && !ctrl->active) return;
+  count_run(ctrl, tkid);
+  const int64_t V = L.V;
+  const int64_t s = (int64_t)blockIdx.x * NT + threadIdx.x;
+  double th = 0.0, f = 0.0;
+  if (s < V) {
+    int c[4];
+    site_coords(L, s, c);
+    cx<T> B[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) B[e] = {0, 0};
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      const int64_t sb = site_back(L, s, mu, c[mu]);
+      const T *plane = U + (int64_t)mu * 9 * V * 2;
+#pragma unroll
+      for (int e = 0; e < 9; ++e) {
+        const cx<T> here = ldg(plane, (int64_t)e * V + s);
+        const cx<T> back = ldg(plane, (int64_t)e * V + sb);
+        B[e] = B[e] + (back - here);
+      }
+      // F partial: Re Tr U_mu(x), summed in double
+      f += (double)ldg(plane, s).r + (double)ldg(plane, 4 * V + s).r + (double)ldg(plane, 8 * V + s).r;
+    }
+    // anti-Hermitian part: Delta_ij = B_ij - conj(B_ji); diagonal 2i Im B_ii, then remove trace/3
+    const cx<T> d01 = B[1] - conjg(B[3]);
+    const cx<T> d02 = B[2] - conjg(B[6]);
+    const cx<T> d12 = B[5] - conjg(B[7]);
+    const T i0 = 2 * B[0].i, i1 = 2 * B[4].i, i2 = 2 * B[8].i;
+    const T m = (i0 + i1 + i2) / (T)3;
+    const T a0 = i0 - m, a1 = i1 - m, a2 = i2 - m;
+    th = (double)a0 * a0 + (double)a1 * a1 + (double)a2 * a2 +
+         2.0 * ((double)norm2(d01) + (double)norm2(d02) + (double)norm2(d12));
+    st(P, s, d01);
+    st(P, V + s, d02);
+    st(P, 2 * V + s, d12);
+    st(P, 3 * V + s, mkc(a0, a1));
+  }
+  reduce_and_finalize<NT>(th, f, partials, ctrl, V, counts_update);
+}
+
+// Rebuild the full anti-Hermitian traceless matrix from the packed fields, scaled by a.
+template <typename T> __device__ __forceinline__ void unpack_scaled(const T *P, int64_t V, int64_t s, T a, m3<T> &m) {
+  const cx<T> p0 = ldg(P, s), p1 = ldg(P, V + s), p2 = ldg(P, 2 * V + s), p3 = ldg(P, 3 * V + s);
+  m.e[0] = {0, a * p3.r};
+  m.e[4] = {0, a * p3.i};
+  m.e[8] = {0, -a * (p3.r + p3.i)};
+  m.e[1] = scale(p0, a);
+  m.e[2] = scale(p1, a);
+  m.e[5] = scale(p2, a);
+  m.e[3] = {-a * p0.r, a * p0.i};  // -conj(a p0)
+  m.e[6] = {-a * p1.r, a * p1.i};
+  m.e[7] = {-a * p2.r, a * p2.i};
+}
+
+// ---------------------------------------------------------------------------------------------
+// a6: g(x) = SU(3)-projection of [1 + (alpha/2) Delta-tilde(x)] (Eq. 2 expanded to first order in
+// alpha, then reunitarized).
+// ---------------------------------------------------------------------------------------------
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_gauge(const T *__restrict__ P, T *__restrict__ G, T half_alpha, int64_t V,
+                                             const Ctrl *ctrl, int check_active, int tkid) {
+  if (check_active && !ctrl->active) return;
+  count_run(ctrl, tkid);
+  const int64_t s = (int64_t)blockIdx.x * NT + threadIdx.x;
+  if (s >= V) return;
+  m3<T> g;
+  unpack_scaled(P, V, s, half_alpha, g);
+  g.e[0].r += 1;
+  g.e[4].r += 1;
+  g.e[8].r += 1;
+  reunitarize(g);
+#pragma unroll
+  for (int e = 0; e < 9; ++e) st(G, (int64_t)e * V + s, g.e[e]);
+}
+
+// ---------------------------------------------------------------------------------------------
+// a7: U_mu(x) -> g(x) U_mu(x) g^dagger(x + mu) for the four directions.
+// ---------------------------------------------------------------------------------------------
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_update(T *__restrict__ U, const T *__restrict__ G, Lattice L, const Ctrl *ctrl,
+                                              int check_active, int tkid) {
+  if (check_active && !ctrl->active) return;
+  count_run(ctrl, tkid);
+  const int64_t V = L.V;
+  const int64_t s = (int64_t)blockIdx.x * NT + threadIdx.x;
+  if (s >= V) return;
+  int c[4];
+  site_coords(L, s, c);
+  m3<T> gx;
+#pragma unroll
+  for (int e = 0; e < 9; ++e) gx.e[e] = ldg(G, (int64_t)e * V + s);
+#pragma unroll 1
+  for (int mu = 0; mu < 4; ++mu) {
+    const int64_t sf = site_fwd(L, s, mu, c[mu]);
+    T *plane = U + (int64_t)mu * 9 * V * 2;
+    m3<T> u, gy, t;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+      u.e[e] = ld(plane, (int64_t)e * V + s);
+      gy.e[e] = ldg(G, (int64_t)e * V + sf);
+    }
+    mul(gx, u, t);
+    mul_adj(t, gy, u);
+#pragma unroll
+    for (int e = 0; e < 9; ++e) st(plane, (int64_t)e * V + s, u.e[e]);
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Layout conversions between the caller's array-of-structures links / site fields (double) and the
+// working planes (T). These run once per load/store, not in the loop.
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void k_aos_to_planes(const double *__restrict__ A, T *__restrict__ Pl, int64_t V, int nmat) {
+  // A: nmat*V matrices of 9 complex; Pl: planes [(m*9 + e)*V + s]
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)nmat * V) return;
+  const int64_t m = idx / V, s = idx - m * V;
+  const double2 *src = reinterpret_cast<const double2 *>(A) + idx * 9;
+#pragma unroll
+  for (int e = 0; e < 9; ++e) {
+    const double2 v = src[e];
+    st(Pl, (m * 9 + e) * V + s, mkc((T)v.x, (T)v.y));
+  }
+}
+
+template <typename T>
+__global__ void k_planes_to_aos(const T *__restrict__ Pl, double *__restrict__ A, int64_t V, int nmat) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)nmat * V) return;
+  const int64_t m = idx / V, s = idx - m * V;
+  double2 *dst = reinterpret_cast<double2 *>(A) + idx * 9;
+#pragma unroll
+  for (int e = 0; e < 9; ++e) {
+    const cx<T> v = ld(Pl, (m * 9 + e) * V + s);
+    dst[e] = make_double2((double)v.r, (double)v.i);
+  }
+}
+
+// Full site matrices (AoS double) <-> packed anti-Hermitian traceless fields (planes, T).
+template <typename T> __global__ void k_pack_antiherm(const double *__restrict__ A, T *__restrict__ P, int64_t V) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  const double2 *m = reinterpret_cast<const double2 *>(A) + s * 9;
+  st(P, s, mkc((T)m[1].x, (T)m[1].y));
+  st(P, V + s, mkc((T)m[2].x, (T)m[2].y));
+  st(P, 2 * V + s, mkc((T)m[5].x, (T)m[5].y));
+  st(P, 3 * V + s, mkc((T)m[0].y, (T)m[4].y));
+}
+
+template <typename T> __global__ void k_unpack_antiherm(const T *__restrict__ P, double *__restrict__ A, int64_t V) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  m3<T> m;
+  unpack_scaled(P, V, s, (T)1, m);
+  double2 *dst = reinterpret_cast<double2 *>(A) + s * 9;
+#pragma unroll
+  for (int e = 0; e < 9; ++e) dst[e] = make_double2((double)m.e[e].r, (double)m.e[e].i);
+}
+
+// Average plaquette partials: (1/3) Re Tr U_mu(x) U_nu(x+mu) U_mu^+(x+nu) U_nu^+(x) over mu < nu.
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_plaquette(const T *__restrict__ U, double *partials, Lattice L) {
+  const int64_t V = L.V;
+  const int64_t s = (int64_t)blockIdx.x * NT + threadIdx.x;
+  double acc = 0.0;
+  if (s < V) {
+    int c[4];
+    site_coords(L, s, c);
+    for (int mu = 0; mu < 4; ++mu)
+      for (int nu = mu + 1; nu < 4; ++nu) {
+        const int64_t smu = site_fwd(L, s, mu, c[mu]), snu = site_fwd(L, s, nu, c[nu]);
+        m3<T> a, b, t, w;
+        for (int e = 0; e < 9; ++e) {
+          a.e[e] = ldg(U + (int64_t)mu * 9 * V * 2, (int64_t)e * V + s);
+          b.e[e] = ldg(U + (int64_t)nu * 9 * V * 2, (int64_t)e * V + smu);
+        }
+        mul(a, b, t);  // U_mu(x) U_nu(x+mu)
+        for (int e = 0; e < 9; ++e) {
+          a.e[e] = ldg(U + (int64_t)mu * 9 * V * 2, (int64_t)e * V + snu);
+          b.e[e] = ldg(U + (int64_t)nu * 9 * V * 2, (int64_t)e * V + s);
+        }
+        mul(b, a, w);  // U_nu(x) U_mu(x+nu)
+        // Re Tr[t w^+] = sum_ij Re t_ij conj(w_ij)
+        for (int e = 0; e < 9; ++e) acc += (double)t.e[e].r * w.e[e].r + (double)t.e[e].i * w.e[e].i;
+      }
+  }
+  double dummy = 0.0;
+  block_sum2<NT>(acc, dummy);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+}  // namespace lgf

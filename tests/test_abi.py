@@ -1,0 +1,64 @@
+"""The C-ABI library loads and exports every entry point the headers declare (no GPU needed; no
+compute call is made)."""
+import ctypes
+import glob
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SO = os.path.join(ROOT, "paper_1210_8018_gb300", "liblgf.so")
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(lgf_\w+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(SO):
+        import importlib.util
+        spec = importlib.util.spec_from_file_location("_b", os.path.join(ROOT, "paper_1210_8018_gb300", "_build.py"))
+        mod = importlib.util.module_from_spec(spec)
+        spec.loader.exec_module(mod)
+        mod.build()
+    return ctypes.CDLL(SO)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["lgf_create", "lgf_fix", "lgf_measure", "lgf_destroy", "lgf_last_error", "lgf_load",
+                     "lgf_iterate", "lgf_store", "lgf_delta", "lgf_filter", "lgf_gauge", "lgf_update"]:
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", SO], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (lgf_\w+)", out))
+    assert set(declared_functions()) <= exported
+
+
+def test_host_only_calls(lib):
+    import paper_1210_8018_gb300 as lgf
+    o = lgf.Options()
+    lgf._lib.lgf_default_options(ctypes.byref(o))
+    assert o.precision == lgf.FP64 and o.theta_switch == 1e-8 and o.reunit_period == 16 and o.max_iter == 100000
+    assert isinstance(lgf._lib.lgf_last_error(None), bytes)
+
+
+def test_no_oracle_in_product_path():
+    """The product path (package and library sources) never refers to the oracle."""
+    for path in glob.glob(os.path.join(ROOT, "paper_1210_8018_gb300", "**", "*"), recursive=True):
+        if os.path.isfile(path) and path.endswith((".py", ".cu", ".cuh", ".h")):
+            src = open(path).read()
+            assert "import oracle" not in src and "oracle." not in src and "liboracle" not in src, path

@@ -1,0 +1,90 @@
+"""The float and mixed-precision schedules against the FP64 oracle: float single steps to float
+accuracy, and a mixed fix that reaches theta < 1e-15 in double precision with links that stay exactly
+gauge-equivalent to the input (plaquette and Wilson loops to 1e-14)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_common import assert_matrix_close
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lgf():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_1210_8018_gb300 as m
+    return m
+
+
+def dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+@pytest.mark.parametrize("dims", [(8, 8, 8, 8), (6, 4, 8, 10)])
+def test_fp32_steps(lgf, dims):
+    """Float steps: error bounded by float roundoff (u32 = 6e-8) times small constants."""
+    U = synth.config(dims, 41, 0.6)
+    D = oracle.delta(U)
+    Dt = oracle.fourier_filter(D)
+    g = oracle.gauge_field(Dt, 0.08)
+    with lgf.Lattice(dims) as lat:
+        out = np.empty_like(D)
+        th, F = lat.delta(U, out, "fp32")
+        assert_matrix_close(out, D, rtol=2e-6)
+        assert abs(F - oracle.functional(U)) < 1e-6
+        lat.filter(D, out, "fp32")
+        assert_matrix_close(out, Dt, rtol=5e-6, scale=float(np.abs(Dt).max()))
+        lat.gauge(Dt, 0.08, out, "fp32")
+        assert_matrix_close(out, g, rtol=1e-6)
+        U2 = U.copy()
+        lat.update(U2, g, "fp32")
+        assert_matrix_close(U2, oracle.gauge_transform(U, g), rtol=2e-6)
+
+
+@pytest.mark.parametrize("dims,seed,eps", [((8, 8, 8, 8), 1, 0.3), ((16, 16, 16, 16), 7, 0.6)])
+def test_mixed_fix(lgf, dims, seed, eps):
+    U = synth.config(dims, seed, eps)
+    Ud = dev(U)
+    with lgf.Lattice(dims) as lat:
+        r = lat.fix(Ud, 0.08, 1e-15, "mixed", history_len=4000)
+        m = lat.measure(Ud)
+    Uf = Ud.cpu().numpy()
+    assert r["converged"] and r["theta"] < 1e-15
+    assert m["theta"] < 1e-15 and abs(m["F"] - r["F"]) < 1e-14
+    # exact gauge equivalence with the input (double handover from the saved input)
+    for R, T in [(1, 1), (1, 2), (2, 2)]:
+        assert abs(oracle.wilson_loop(Uf, R, T) - oracle.wilson_loop(U, R, T)) < 1e-14
+    assert oracle.unitarity_violation(Uf) < 1e-13
+    h = r["history"][: r["iters"] + 1]
+    assert np.all(np.diff(h[:, 1]) > -1e-6)  # float stage: F rises up to float roundoff
+    # oracle values at the fixed links agree with the library's
+    assert abs(oracle.theta(oracle.delta(Uf)) - r["theta"]) < 1e-16 + 1e-12 * r["theta"]
+    assert abs(oracle.functional(Uf) - r["F"]) < 1e-12
+
+
+def test_mixed_store_mid_float_stage_is_gauge_equivalent(lgf):
+    dims = (8, 8, 4, 6)
+    U = synth.config(dims, 9, 0.6)
+    with lgf.Lattice(dims) as lat:
+        lat.load(U, "mixed")
+        r = lat.iterate(5, 0.08, 1e-15, theta_switch=1e-30)
+        assert r["iters"] == 5
+        Us = np.empty_like(U)
+        lat.store(Us)
+    assert abs(oracle.plaquette(Us) - oracle.plaquette(U)) < 1e-14
+    assert oracle.unitarity_violation(Us) < 1e-13
+    # the rebuilt links carry the float stage's progress
+    th0 = oracle.theta(oracle.delta(U))
+    assert oracle.theta(oracle.delta(Us)) < 0.5 * th0
+
+
+def test_fp32_precision_fix_reaches_float_floor(lgf):
+    dims = (8, 8, 8, 8)
+    U = synth.config(dims, 1, 0.3)
+    with lgf.Lattice(dims) as lat:
+        r = lat.fix(U.copy(), 0.08, 1e-9, "fp32", max_iter=500)
+    assert r["converged"] and r["theta"] < 1e-9
