@@ -145,6 +145,27 @@ lgf_status lgf_enable_timing(lgf_ctx *ctx, int enable);
 lgf_status lgf_kernel_times(lgf_ctx *ctx, const char **name, long *launches, double *ms, int cap,
                             int *count);
 
+/* ---- Measurement without allocation. The paper has no counterpart: this entry point exists for
+ * callers that cannot allocate device memory when they need Delta, theta and F -- a framework whose
+ * pool owns all device memory and rejects or starves other allocations, a loop that must not stall on
+ * cudaMalloc (which may synchronize the device), or an out-of-memory handler that has nothing left to
+ * allocate. It needs no context: every input and output is the caller's, and the only scratch (per-block
+ * partial sums of the reduction and a counter, 1 MiB) is a fixed array inside the library's device
+ * image. The call allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
+ *   links     device pointer, the links layout above, 16-byte aligned
+ *   delta     device pointer to V*9 complex doubles (site-field layout) for Delta(x), or NULL
+ *   theta_F   device pointer to 2 doubles: theta (Eq. 4) and F (Eq. 1 at g = 1)
+ *   stream    cudaStream_t to issue on (NULL = the legacy default stream); the call does not wait:
+ *             the outputs are complete when the stream reaches that point
+ * Limits: V = Nx*Ny*Nz*Nt <= 16777216 (2^24, e.g. 64^4); extents as for lgf_create. Larger lattices,
+ * host pointers or bad extents return LGF_EINVAL with a message from lgf_last_error(NULL).
+ * The first call on a device looks up the device address of the scratch array (once per device, with
+ * that device current); make that first call before any stream capture. All calls on a device share
+ * the scratch array, which keeps the last call's contents (the counter is cleared by each call): calls
+ * that overlap on the GPU race and give wrong results, so order them on one stream. */
+lgf_status lgf_delta_noalloc(const double *links, int Nx, int Ny, int Nz, int Nt, double *delta, double *theta_F,
+                             void *stream);
+
 #ifdef __cplusplus
 }
 #endif

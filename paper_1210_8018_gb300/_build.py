@@ -4,7 +4,7 @@ import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SO = os.path.join(HERE, "liblgf.so")
-SOURCES = [os.path.join(HERE, "csrc", "lgf.cu")]
+SOURCES = [os.path.join(HERE, "csrc", "lgf.cu"), os.path.join(HERE, "csrc", "noalloc.cu")]
 DEPS = [os.path.join(HERE, "csrc", f) for f in os.listdir(os.path.join(HERE, "csrc"))] + [
     os.path.join(os.path.dirname(HERE), "include", "lgf.h")]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",

@@ -123,6 +123,7 @@ struct lgf_ctx {
 namespace {
 
 thread_local std::string g_last_static_error;
+thread_local const char *g_static_literal = nullptr;  // a static message set without allocating
 
 lgf_status fail(lgf_ctx *c, lgf_status st, const std::string &msg) {
   if (c) {
@@ -130,6 +131,7 @@ lgf_status fail(lgf_ctx *c, lgf_status st, const std::string &msg) {
     if (st == LGF_ECUDA) c->poisoned = true;
   } else {
     g_last_static_error = msg;
+    g_static_literal = nullptr;
   }
   return st;
 }
@@ -537,6 +539,11 @@ lgf_status check_ctx(lgf_ctx *ctx) {
 
 }  // namespace
 
+// Library-internal (not exported): lets other translation units of the library report a message
+// through lgf_last_error(NULL).
+// msg must be a string with static storage (it is kept by pointer; nothing is allocated). NULL clears it.
+__attribute__((visibility("hidden"))) void lgf_set_static_error(const char *msg) { g_static_literal = msg; }
+
 // ============================================== C ABI ===============================================
 extern "C" {
 
@@ -637,7 +644,7 @@ void lgf_destroy(lgf_ctx *ctx) {
 }
 
 const char *lgf_last_error(const lgf_ctx *ctx) {
-  if (!ctx) return g_last_static_error.c_str();
+  if (!ctx) return g_static_literal ? g_static_literal : g_last_static_error.c_str();
   return ctx->err.c_str();
 }
 
