@@ -70,12 +70,13 @@ def algorithmic(kernel, dims):
         "fft_t_filter": (8 * es, 4 * (2 * 5 * lg["t"] + 6)),
         # packed Delta-tilde read, g written
         "gauge_g": ((4 + 9) * es, 160),
-        # links read and written, g read (neighbours are the same data); 8 SU(3) products
-        "gauge_update": ((36 + 36 + 9) * es, 8 * 216),
-        "gauge_update_accumulate": ((36 + 36 + 9 + 18) * es, 9 * 216),
+        # links read and written, g read (neighbours are the same data); per link rows 0-1 of
+        # g U (18 complex MACs) and of (g U) g^+ (18), row 2 by a cross product: 168 FMA = 336 flop
+        "gauge_update": ((36 + 36 + 9) * es, 4 * 336),
+        "gauge_update_accumulate": ((36 + 36 + 9 + 18) * es, 4 * 336 + 216),
         "reunitarize": (5 * 9 * 2 * 8, 5 * 170),
         "gacc_to_double": (9 * 8 + 9 * 16, 170),
-        "handover_transform": (36 * 16 * 2 + 9 * 16, 8 * 216),
+        "handover_transform": (36 * 16 * 2 + 9 * 16, 8 * 216),  # full products (8 x 27 complex MACs)
         "to_planes": (36 * 16 + 36 * es, 0),
         "from_planes": (36 * es + 36 * 16, 0),
         "set_identity": (9 * 8, 0),

@@ -1,0 +1,239 @@
+// fft_fixed.cuh -- FFT passes specialised at compile time for the common axis lengths
+// (8, 16, 24, 32, 48, 64), used by the planner whenever the lattice allows; other lengths use the
+// generic passes of fft.cuh. Same mathematics as fft.cuh (in-place mixed-radix DIF forward with a
+// digit-reversed spectrum, exact DIT inverse, filter w = p^2_max/(V p^2) fused into the last forward
+// pass), with these differences:
+//   * every extent, stride inside the tile and radix is a constant, so index arithmetic folds away;
+//   * tiles live in shared memory with an odd row pitch and the pencil index varies fastest across
+//     threads, so every stage is free of bank conflicts for 8- and 16-byte elements;
+//   * each thread issues all of its global loads before any shared-memory store;
+//   * the filter pass holds the four packed fields of its columns at once, so the weight of a site
+//     is computed once (in the pass's own precision) and applied to all four.
+#pragma once
+#include "fft.cuh"
+
+namespace lgf {
+
+// Radix plans, identical to the host planner's greedy factorisation (8s first, then 4, 2, 3, 5).
+template <int... Rs> struct RadixList {};
+template <int N> struct PlanOf;
+template <> struct PlanOf<8> { using type = RadixList<8>; };
+template <> struct PlanOf<16> { using type = RadixList<8, 2>; };
+template <> struct PlanOf<24> { using type = RadixList<8, 3>; };
+template <> struct PlanOf<32> { using type = RadixList<8, 4>; };
+template <> struct PlanOf<48> { using type = RadixList<8, 2, 3>; };
+template <> struct PlanOf<64> { using type = RadixList<8, 8>; };
+
+// One DIF (or inverse DIT) stage of block length L and radix R along a tile axis of length N whose
+// elements are `estride` apart; NPEN pencils whose first elements are `pstride` apart.
+template <typename T, int N, int L, int R, bool INV, int NPEN, int NT>
+__device__ __forceinline__ void fx_stage(cx<T> *tile, const cx<T> *tw, int estride, int pstride) {
+  constexpr int M = L / R;
+  constexpr int NB = N / R;
+  constexpr int TWSTEP = N / L;
+  constexpr int ITEMS = NPEN * NB;
+#pragma unroll 2
+  for (int w = threadIdx.x; w < ITEMS; w += NT) {
+    const int pen = w % NPEN;
+    const int beta = w / NPEN;
+    const int blk = beta / M, j = beta % M;
+    cx<T> *p = tile + pen * pstride + (blk * L + j) * estride;
+    cx<T> v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = p[r * M * estride];
+    if constexpr (!INV) {
+      dft<T, R, false>(v);
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[r] = v[r] * tw[j * r * TWSTEP];
+    } else {
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[r] = v[r] * conjg(tw[j * r * TWSTEP]);
+      dft<T, R, true>(v);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) p[r * M * estride] = v[r];
+  }
+}
+
+template <typename T, int N, int L, int NPEN, int NT, int R, int... Rest>
+__device__ __forceinline__ void fx_forward(cx<T> *tile, const cx<T> *tw, int estride, int pstride) {
+  fx_stage<T, N, L, R, false, NPEN, NT>(tile, tw, estride, pstride);
+  __syncthreads();
+  if constexpr (sizeof...(Rest) > 0) fx_forward<T, N, L / R, NPEN, NT, Rest...>(tile, tw, estride, pstride);
+}
+template <typename T, int N, int L, int NPEN, int NT, int R, int... Rest>
+__device__ __forceinline__ void fx_inverse(cx<T> *tile, const cx<T> *tw, int estride, int pstride) {
+  if constexpr (sizeof...(Rest) > 0) fx_inverse<T, N, L / R, NPEN, NT, Rest...>(tile, tw, estride, pstride);
+  fx_stage<T, N, L, R, true, NPEN, NT>(tile, tw, estride, pstride);
+  __syncthreads();
+}
+template <typename T, int N, int NPEN, int NT, bool INV, int... Rs>
+__device__ __forceinline__ void fx_axis_impl(RadixList<Rs...>, cx<T> *tile, const cx<T> *tw, int estride,
+                                             int pstride) {
+  if constexpr (!INV) fx_forward<T, N, N, NPEN, NT, Rs...>(tile, tw, estride, pstride);
+  else fx_inverse<T, N, N, NPEN, NT, Rs...>(tile, tw, estride, pstride);
+}
+template <typename T, int N, int NPEN, int NT, bool INV>
+__device__ __forceinline__ void fx_axis(cx<T> *tile, const cx<T> *tw, int estride, int pstride) {
+  fx_axis_impl<T, N, NPEN, NT, INV>(typename PlanOf<N>::type{}, tile, tw, estride, pstride);
+}
+
+template <typename T, int N> __device__ __forceinline__ void load_twiddles(cx<T> *dst, const void *src) {
+  const cx<T> *s = reinterpret_cast<const cx<T> *>(src);
+  for (int k = threadIdx.x; k < N; k += blockDim.x) dst[k] = s[k];
+}
+
+// ---------------------------------------------------------------------------------------------
+// xy plane pass: the 2D transform of one (z, t) plane of one packed field. Tile [NY][NX] with row
+// pitch NX + 1. blockIdx.x = plane, blockIdx.y = field.
+// ---------------------------------------------------------------------------------------------
+template <typename T, int NX, int NY, bool INV, int NT>
+__global__ void __launch_bounds__(NT) k_fx_plane(T *__restrict__ data, int64_t V, FFTTables tb, const Ctrl *ctrl,
+                                                int check_active, int tkid) {
+  if (check_active && !ctrl->active) return;
+  count_run(ctrl, tkid);
+  constexpr int P = NX + 1;
+  constexpr int NEL = NX * NY;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T> *tile = reinterpret_cast<cx<T> *>(smem_raw);
+  cx<T> *twx = tile + NY * P;
+  cx<T> *twy = twx + NX;
+  load_twiddles<T, NX>(twx, tb.tw[0]);
+  load_twiddles<T, NY>(twy, tb.tw[1]);
+  const cx<T> *src = reinterpret_cast<const cx<T> *>(data + (int64_t)blockIdx.y * V * 2) + (int64_t)blockIdx.x * NEL;
+  constexpr int PER = (NEL + NT - 1) / NT;
+  cx<T> reg[PER];
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const int e = threadIdx.x + k * NT;
+    if (e < NEL) {
+      const typename vec2<T>::type v = __ldg(reinterpret_cast<const typename vec2<T>::type *>(src) + e);
+      reg[k] = {v.x, v.y};
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const int e = threadIdx.x + k * NT;
+    if (e < NEL) tile[(e / NX) * P + (e % NX)] = reg[k];
+  }
+  __syncthreads();
+  if (!INV) {
+    fx_axis<T, NX, NY, NT, false>(tile, twx, 1, P);  // along x: pencils are rows
+    fx_axis<T, NY, NX, NT, false>(tile, twy, P, 1);  // along y: pencils are columns
+  } else {
+    fx_axis<T, NY, NX, NT, true>(tile, twy, P, 1);
+    fx_axis<T, NX, NY, NT, true>(tile, twx, 1, P);
+  }
+  cx<T> *dst = reinterpret_cast<cx<T> *>(data + (int64_t)blockIdx.y * V * 2) + (int64_t)blockIdx.x * NEL;
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const int e = threadIdx.x + k * NT;
+    if (e < NEL) {
+      const cx<T> v = tile[(e / NX) * P + (e % NX)];
+      typename vec2<T>::type o;
+      o.x = v.r;
+      o.y = v.i;
+      reinterpret_cast<typename vec2<T>::type *>(dst)[e] = o;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Column pass along one lattice axis of length N (z or t): a tile of N rows (row stride `rstride`
+// complex elements) by C contiguous columns, pitch C + 1. Block b covers columns
+// (b % ncb) * C .. + C of outer slice b / ncb (outer stride `ostride`).
+//   MODE 0: forward (one field per block, blockIdx.y = field)
+//   MODE 1: inverse (one field per block)
+//   MODE 2: forward + filter + inverse, all four fields per block; this pass must be the last axis
+//           (t), so that the columns enumerate x, y, z.
+// ---------------------------------------------------------------------------------------------
+template <typename T, int N, int C, int MODE, int NT>
+__global__ void __launch_bounds__(NT) k_fx_cols(T *__restrict__ data, int64_t V, int64_t rstride, int ncb,
+                                               int64_t ostride, FFTTables tb, const Ctrl *ctrl, int check_active,
+                                               int tkid, int twmu) {
+  if (check_active && !ctrl->active) return;
+  count_run(ctrl, tkid);
+  constexpr int P = C + 1;
+  constexpr int NF = MODE == 2 ? 4 : 1;
+  constexpr int TILE = N * P;
+  constexpr int NEL = N * C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T> *tile = reinterpret_cast<cx<T> *>(smem_raw);
+  cx<T> *tw = tile + NF * TILE;
+  load_twiddles<T, N>(tw, tb.tw[twmu]);
+  const int b = blockIdx.x;
+  const int64_t col0 = (int64_t)(b % ncb) * C;
+  const int64_t base = col0 + (int64_t)(b / ncb) * ostride;
+  constexpr int PER = (NEL + NT - 1) / NT;
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    const int field = MODE == 2 ? f : (int)blockIdx.y;
+    const cx<T> *src = reinterpret_cast<const cx<T> *>(data + (int64_t)field * V * 2);
+    cx<T> reg[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int e = threadIdx.x + k * NT;
+      if (e < NEL) {
+        const int n = e / C, c = e % C;
+        const typename vec2<T>::type v =
+            __ldg(reinterpret_cast<const typename vec2<T>::type *>(src) + base + n * rstride + c);
+        reg[k] = {v.x, v.y};
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int e = threadIdx.x + k * NT;
+      if (e < NEL) tile[f * TILE + (e / C) * P + (e % C)] = reg[k];
+    }
+  }
+  __syncthreads();
+  // along the rows: element stride P, pencils (columns) stride 1; the four fields are stacked, so
+  // they form NF*C pencils whose bases are TILE apart: handle each field in turn.
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    if (MODE == 1) fx_axis<T, N, C, NT, true>(tile + f * TILE, tw, P, 1);
+    else fx_axis<T, N, C, NT, false>(tile + f * TILE, tw, P, 1);
+  }
+  if constexpr (MODE == 2) {
+    // weight of each (row, column): w = p2max / (V (p2_xyz(column) + p2_t(row))), 0 at k = 0
+    __shared__ T sxyz[C];
+    for (int c = threadIdx.x; c < C; c += NT) {
+      const int64_t q = col0 + c;
+      const int x = (int)(q % tb.n[0]);
+      const int64_t r = q / tb.n[0];
+      const int y = (int)(r % tb.n[1]);
+      const int z = (int)(r / tb.n[1]);
+      sxyz[c] = (T)(__ldg(tb.p2part[0] + x) + __ldg(tb.p2part[1] + y) + __ldg(tb.p2part[2] + z));
+    }
+    __syncthreads();
+    const T wscale = (T)tb.wscale;
+    for (int e = threadIdx.x; e < NEL; e += NT) {
+      const int n = e / C, c = e % C;
+      const T p2 = sxyz[c] + (T)__ldg(tb.p2part[3] + n);
+      const T w = p2 == (T)0 ? (T)0 : wscale / p2;
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        cx<T> &v = tile[f * TILE + n * P + c];
+        v = scale(v, w);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int f = 0; f < 4; ++f) fx_axis<T, N, C, NT, true>(tile + f * TILE, tw, P, 1);
+  }
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    const int field = MODE == 2 ? f : (int)blockIdx.y;
+    cx<T> *dst = reinterpret_cast<cx<T> *>(data + (int64_t)field * V * 2);
+    for (int e = threadIdx.x; e < NEL; e += NT) {
+      const int n = e / C, c = e % C;
+      const cx<T> v = tile[f * TILE + n * P + c];
+      typename vec2<T>::type o;
+      o.x = v.r;
+      o.y = v.i;
+      reinterpret_cast<typename vec2<T>::type *>(dst)[base + n * rstride + c] = o;
+    }
+  }
+}
+
+}  // namespace lgf

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <type_traits>
@@ -13,6 +14,8 @@
 
 #include "../../include/lgf.h"
 #include "fft.cuh"
+#include "fft_fixed.cuh"
+#include "autograd_kernels.cuh"
 #include "mixed_kernels.cuh"
 #include "site_kernels.cuh"
 
@@ -60,7 +63,13 @@ struct Pass {
   int kid;
   size_t smem;
   int threads;
+  // specialised passes (fft_fixed.cuh): kind 1 = xy plane, kind 2 = columns along z or t
+  int kind = 0;
+  int N = 0, C = 0, mode = 0, twmu = 0, ncb = 0, nblocks = 0;
+  int64_t rstride = 0, ostride = 0;
 };
+constexpr int kFixedThreads = 256;
+bool fixed_len(int n) { return n == 8 || n == 16 || n == 24 || n == 32 || n == 48 || n == 64; }
 
 template <typename T> struct State {
   T *U = nullptr;  // links, planes
@@ -89,6 +98,8 @@ struct lgf_ctx {
   double wscale = 0;
   AxisFFT ax[4];
 
+  double *Wev = nullptr;    // differentiable functional: eigenvectors of omega (9 planes)
+  double *lam = nullptr;    // and its eigenvalues (3 planes of doubles)
   double *U0 = nullptr;     // mixed: input links (double planes) for the handover
   float *Gacc = nullptr;    // mixed/float: accumulated gauge transformation (9 float planes)
   double *staging = nullptr;  // AoS double buffer for host inputs / outputs and single steps
@@ -108,6 +119,7 @@ struct lgf_ctx {
   int load_prec = 0;    // the precision it was loaded with
   int stage = -1;       // LGF_FP64 or LGF_FP32: precision of the live working links
   int since_reunit = 0;
+  bool generic_fft = false;  // force the generic FFT passes (tests compare the two families)
   double prev_theta = 0;  // theta and iteration count at the previous chunk boundary
   int prev_iters = 0;
 
@@ -234,8 +246,85 @@ template <typename T> lgf_status alloc(lgf_ctx *ctx, T **p, size_t count) {
   return LGF_OK;
 }
 
+// Kernel pointers of the specialised passes.
+template <typename T, bool INV> const void *plane_kernel(int n) {
+  switch (n) {
+    case 8: return (const void *)k_fx_plane<T, 8, 8, INV, kFixedThreads>;
+    case 16: return (const void *)k_fx_plane<T, 16, 16, INV, kFixedThreads>;
+    case 24: return (const void *)k_fx_plane<T, 24, 24, INV, kFixedThreads>;
+    case 32: return (const void *)k_fx_plane<T, 32, 32, INV, kFixedThreads>;
+    case 48: return (const void *)k_fx_plane<T, 48, 48, INV, kFixedThreads>;
+    default: return (const void *)k_fx_plane<T, 64, 64, INV, kFixedThreads>;
+  }
+}
+template <typename T, int C, int MODE> const void *cols_kernel(int n) {
+  switch (n) {
+    case 8: return (const void *)k_fx_cols<T, 8, C, MODE, kFixedThreads>;
+    case 16: return (const void *)k_fx_cols<T, 16, C, MODE, kFixedThreads>;
+    case 24: return (const void *)k_fx_cols<T, 24, C, MODE, kFixedThreads>;
+    case 32: return (const void *)k_fx_cols<T, 32, C, MODE, kFixedThreads>;
+    case 48: return (const void *)k_fx_cols<T, 48, C, MODE, kFixedThreads>;
+    default: return (const void *)k_fx_cols<T, 64, C, MODE, kFixedThreads>;
+  }
+}
+template <typename T> const void *fixed_kernel(const Pass &p) {
+  constexpr int C = sizeof(T) == 8 ? 16 : 32;
+  if (p.kind == 1) return p.mode == 0 ? plane_kernel<T, false>(p.N) : plane_kernel<T, true>(p.N);
+  if (p.mode == 0) return cols_kernel<T, C, 0>(p.N);
+  if (p.mode == 1) return cols_kernel<T, C, 1>(p.N);
+  return cols_kernel<T, C, 2>(p.N);
+}
+
+// Specialised plan (5 passes: xy forward, z forward, t forward + filter + inverse, z inverse,
+// xy inverse) when every extent is one of the fixed lengths and Nx == Ny; false otherwise.
+template <typename T> bool plan_fixed(lgf_ctx *ctx, State<T> &S) {
+  const int Nx = ctx->n[0], Ny = ctx->n[1], Nz = ctx->n[2], Nt = ctx->n[3];
+  for (int mu = 0; mu < 4; ++mu)
+    if (!fixed_len(ctx->n[mu])) return false;
+  if (Nx != Ny) return false;
+  const int C = sizeof(T) == 8 ? 16 : 32;
+  const int64_t Nxy = (int64_t)Nx * Ny, Nxyz = Nxy * Nz;
+  if (Nxy % C || Nxyz % C) return false;
+  const size_t es = sizeof(cx<T>);
+  auto plane = [&](int mode, int kid) {
+    Pass p{};
+    p.kind = 1;
+    p.N = Nx;
+    p.mode = mode;
+    p.kid = kid;
+    p.nblocks = Nz * Nt;
+    p.threads = kFixedThreads;
+    p.smem = (size_t)(Ny * (Nx + 1) + Nx + Ny) * es;
+    return p;
+  };
+  auto cols = [&](int N, int mode, int64_t rstride, int ncb, int64_t ostride, int nouter, int twmu, int kid) {
+    Pass p{};
+    p.kind = 2;
+    p.N = N;
+    p.C = C;
+    p.mode = mode;
+    p.kid = kid;
+    p.rstride = rstride;
+    p.ncb = ncb;
+    p.ostride = ostride;
+    p.nblocks = ncb * nouter;
+    p.twmu = twmu;
+    p.threads = kFixedThreads;
+    p.smem = (size_t)((mode == 2 ? 4 : 1) * N * (C + 1) + N) * es;
+    return p;
+  };
+  S.passes.clear();
+  S.passes.push_back(plane(0, KID_FFT_XY_FWD));
+  S.passes.push_back(cols(Nz, 0, Nxy, (int)(Nxy / C), Nxyz, Nt, 2, KID_FFT_Z_FWD));
+  S.passes.push_back(cols(Nt, 2, Nxyz, (int)(Nxyz / C), 0, 1, 3, KID_FFT_T_FILTER));
+  S.passes.push_back(cols(Nz, 1, Nxy, (int)(Nxy / C), Nxyz, Nt, 2, KID_FFT_Z_INV));
+  S.passes.push_back(plane(1, KID_FFT_XY_INV));
+  return true;
+}
+
 // Plan the FFT passes for element size es (bytes per complex number).
 template <typename T> void plan_passes(lgf_ctx *ctx, State<T> &S) {
+  if (!ctx->generic_fft && plan_fixed<T>(ctx, S)) return;
   const int Nx = ctx->n[0], Ny = ctx->n[1], Nz = ctx->n[2], Nt = ctx->n[3];
   const int64_t Nxy = (int64_t)Nx * Ny, Nxyz = Nxy * Nz;
   const size_t es = sizeof(cx<T>);
@@ -342,11 +431,15 @@ template <typename T> lgf_status setup_precision(lgf_ctx *ctx, State<T> &S) {
       S.tables.n[mu] = ctx->n[mu];
     }
     S.tables.wscale = ctx->wscale;
-    for (auto &p : S.passes)
-      if (p.smem > 48 * 1024) {
-        CK(cudaFuncSetAttribute(k_fft_pass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::min<size_t>(ctx->smem_optin, 227 * 1024)));
-        break;
-      }
+    // opt in to the dynamic shared memory each pass needs (the generic kernel: the largest of its passes)
+    size_t generic_max = 0;
+    for (auto &p : S.passes) {
+      if (p.kind == 0) generic_max = std::max(generic_max, p.smem);
+      else if (p.smem > 48 * 1024)
+        CK(cudaFuncSetAttribute(fixed_kernel<T>(p), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
+    }
+    if (generic_max > 48 * 1024)
+      CK(cudaFuncSetAttribute(k_fft_pass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)generic_max));
   }
   return LGF_OK;
 }
@@ -421,9 +514,27 @@ template <typename T> lgf_status launch_delta(lgf_ctx *ctx, State<T> &S, int cou
 template <typename T> lgf_status launch_filter(lgf_ctx *ctx, State<T> &S, T *data, int check_active) {
   for (auto &p : S.passes) {
     TRY(timed_begin(ctx, kid<T>(p.kid)));
-    dim3 grid(p.d.nblocks, 4);
-    k_fft_pass<T><<<grid, p.threads, p.smem, ctx->stream>>>(data, ctx->V, p.d, S.tables, ctx->ctrl, check_active,
-                                                             kid<T>(p.kid));
+    const int tk = kid<T>(p.kid);
+    if (p.kind == 0) {
+      dim3 grid(p.d.nblocks, 4);
+      k_fft_pass<T><<<grid, p.threads, p.smem, ctx->stream>>>(data, ctx->V, p.d, S.tables, ctx->ctrl, check_active,
+                                                               tk);
+    } else if (p.kind == 1) {
+      dim3 grid(p.nblocks, 4);
+      int64_t V = ctx->V;
+      FFTTables tb = S.tables;
+      const Ctrl *c = ctx->ctrl;
+      void *args[] = {&data, &V, &tb, &c, &check_active, (void *)&tk};
+      CK(cudaLaunchKernel(fixed_kernel<T>(p), grid, dim3(p.threads), args, p.smem, ctx->stream));
+    } else {
+      dim3 grid(p.nblocks, p.mode == 2 ? 1 : 4);
+      int64_t V = ctx->V, rs = p.rstride, os = p.ostride;
+      int ncb = p.ncb, twmu = p.twmu;
+      FFTTables tb = S.tables;
+      const Ctrl *c = ctx->ctrl;
+      void *args[] = {&data, &V, &rs, &ncb, &os, &tb, &c, &check_active, (void *)&tk, &twmu};
+      CK(cudaLaunchKernel(fixed_kernel<T>(p), grid, dim3(p.threads), args, p.smem, ctx->stream));
+    }
     CKL();
     TRY(timed_end(ctx));
   }
@@ -583,6 +694,11 @@ lgf_status lgf_create(int Nx, int Ny, int Nz, int Nt, lgf_ctx **out) {
   if (cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking) != cudaSuccess)
     return bail(LGF_ECUDA, "cudaStreamCreate failed");
   ctx->stream = ctx->own_stream;
+  {
+    // LGF_GENERIC_FFT=1 forces the generic FFT passes (used by the tests to check both families)
+    const char *g = std::getenv("LGF_GENERIC_FFT");
+    ctx->generic_fft = g && g[0] == '1';
+  }
   cudaDeviceGetAttribute(&ctx->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
   // p^2 tables (position -> 4 sin^2(pi k / N)) and the filter scale p^2_max / V
   double p2max = 0;
@@ -628,6 +744,8 @@ void lgf_destroy(lgf_ctx *ctx) {
     fr(ctx->p2part[mu]);
   }
   fr(ctx->U0);
+  fr(ctx->Wev);
+  fr(ctx->lam);
   fr(ctx->Gacc);
   fr(ctx->staging);
   fr(ctx->staging2);
@@ -984,6 +1102,61 @@ extern "C" lgf_status lgf_update(lgf_ctx *ctx, double *links, const double *g, i
   if (host) CK(cudaMemcpyAsync(links, ldev, (size_t)4 * V * 144, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->loaded = false;
+  return LGF_OK;
+}
+
+// ------------------------------ differentiable functional ------------------------------
+// Shared set-up of lgf_functional / lgf_functional_grad: links to planes, omega -> g, W, l.
+static lgf_status prepare_functional(lgf_ctx *ctx, const double *links, const double *omega) {
+  TRY(check_ctx(ctx));
+  TRY(ensure_common(ctx));
+  TRY(setup_precision<double>(ctx, ctx->s64));
+  const int64_t V = ctx->V;
+  TRY(alloc(ctx, &ctx->Wev, (size_t)9 * V * 2));
+  TRY(alloc(ctx, &ctx->lam, (size_t)3 * V));
+  const double *ldev = nullptr, *odev = nullptr;
+  TRY(input_ptr(ctx, links, (size_t)4 * V * 144, &ctx->staging, &ctx->staging_bytes, &ldev));
+  TRY(input_ptr(ctx, omega, (size_t)V * 64, &ctx->staging2, &ctx->staging2_bytes, &odev));
+  TRY(to_planes<double>(ctx, ldev, ctx->s64.U, 4));
+  k_expi<NT><<<grid1(V, NT), NT, 0, ctx->stream>>>(odev, ctx->s64.G, ctx->Wev, ctx->lam, V);
+  CKL();
+  ctx->loaded = false;  // the working links were overwritten
+  return LGF_OK;
+}
+
+extern "C" lgf_status lgf_functional(lgf_ctx *ctx, const double *links, const double *omega, double *F,
+                                     double *g_out) {
+  TRY(prepare_functional(ctx, links, omega));
+  const int64_t V = ctx->V;
+  memset(&ctx->ctrl_host, 0, sizeof(Ctrl));
+  TRY(write_ctrl(ctx));
+  k_functional_g<NT><<<ctx->nblocks_site, NT, 0, ctx->stream>>>(ctx->s64.U, ctx->s64.G, ctx->partials, ctx->ctrl,
+                                                                ctx->L);
+  CKL();
+  if (g_out) {
+    double *gdev = nullptr;
+    bool host = false;
+    TRY(output_ptr(ctx, g_out, (size_t)V * 144, &ctx->staging, &ctx->staging_bytes, &gdev, &host));
+    TRY(from_planes<double>(ctx, ctx->s64.G, gdev, 1));
+    if (host) CK(cudaMemcpyAsync(g_out, gdev, (size_t)V * 144, cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  TRY(read_ctrl(ctx));
+  if (F) *F = ctx->ctrl_host.F;
+  return LGF_OK;
+}
+
+extern "C" lgf_status lgf_functional_grad(lgf_ctx *ctx, const double *links, const double *omega, double scale,
+                                          double *grad) {
+  TRY(prepare_functional(ctx, links, omega));
+  const int64_t V = ctx->V;
+  double *gdev = nullptr;
+  bool host = false;
+  TRY(output_ptr(ctx, grad, (size_t)V * 64, &ctx->staging, &ctx->staging_bytes, &gdev, &host));
+  k_functional_grad<NT><<<grid1(V, NT), NT, 0, ctx->stream>>>(ctx->s64.U, ctx->s64.G, ctx->Wev, ctx->lam, gdev,
+                                                              ctx->L, scale);
+  CKL();
+  if (host) CK(cudaMemcpyAsync(grad, gdev, (size_t)V * 64, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
   return LGF_OK;
 }
 

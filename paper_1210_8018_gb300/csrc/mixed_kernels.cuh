@@ -39,8 +39,9 @@ __global__ void __launch_bounds__(NT) k_update_accumulate(float *__restrict__ U,
       u.e[e] = ld(plane, (int64_t)e * V + s);
       gy.e[e] = ldg(G, (int64_t)e * V + sf);
     }
-    mul(gx, u, t);
-    mul_adj(t, gy, u);
+    mul_rows01(gx, u, t);
+    mul_adj_rows01(t, gy, u);
+    complete_row2(u);
 #pragma unroll
     for (int e = 0; e < 9; ++e) st(plane, (int64_t)e * V + s, u.e[e]);
   }

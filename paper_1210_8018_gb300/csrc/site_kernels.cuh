@@ -46,14 +46,15 @@ __device__ __forceinline__ int64_t site_back(const Lattice &L, int64_t s, int mu
 __device__ __forceinline__ int64_t site_fwd(const Lattice &L, int64_t s, int mu, int c) {
   return c == L.n[mu] - 1 ? s - (int64_t)(L.n[mu] - 1) * L.stride[mu] : s + L.stride[mu];
 }
-__device__ __forceinline__ void site_coords(const Lattice &L, int64_t s, int c[4]) {
-  int64_t r = s;
-  c[0] = (int)(r % L.n[0]);
-  r /= L.n[0];
-  c[1] = (int)(r % L.n[1]);
-  r /= L.n[1];
-  c[2] = (int)(r % L.n[2]);
-  c[3] = (int)(r / L.n[2]);
+// Coordinates of site s (V < 2^31 for every lattice that fits in memory, so 32-bit division).
+__device__ __forceinline__ void site_coords(const Lattice &L, int64_t s64, int c[4]) {
+  unsigned r = (unsigned)s64;
+  c[0] = (int)(r % (unsigned)L.n[0]);
+  r /= (unsigned)L.n[0];
+  c[1] = (int)(r % (unsigned)L.n[1]);
+  r /= (unsigned)L.n[1];
+  c[2] = (int)(r % (unsigned)L.n[2]);
+  c[3] = (int)(r / (unsigned)L.n[2]);
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -236,8 +237,10 @@ __global__ void __launch_bounds__(NT) k_update(T *__restrict__ U, const T *__res
       u.e[e] = ld(plane, (int64_t)e * V + s);
       gy.e[e] = ldg(G, (int64_t)e * V + sf);
     }
-    mul(gx, u, t);
-    mul_adj(t, gy, u);
+    // rows 0 and 1 of g(x) U g^+(x+mu) by products, row 2 = conj(row0 x row1) (the result is in SU(3))
+    mul_rows01(gx, u, t);
+    mul_adj_rows01(t, gy, u);
+    complete_row2(u);
 #pragma unroll
     for (int e = 0; e < 9; ++e) st(plane, (int64_t)e * V + s, u.e[e]);
   }

@@ -90,6 +90,38 @@ template <typename T> __device__ __forceinline__ void mul_adj(const m3<T> &a, co
     }
 }
 
+// Rows 0 and 1 of c = a b (row 2 of c is left untouched).
+template <typename T> __device__ __forceinline__ void mul_rows01(const m3<T> &a, const m3<T> &b, m3<T> &c) {
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      cx<T> acc = a.e[3 * i] * b.e[j];
+      acc = cmac(acc, a.e[3 * i + 1], b.e[3 + j]);
+      acc = cmac(acc, a.e[3 * i + 2], b.e[6 + j]);
+      c.e[3 * i + j] = acc;
+    }
+}
+// Rows 0 and 1 of c = a b^dagger.
+template <typename T> __device__ __forceinline__ void mul_adj_rows01(const m3<T> &a, const m3<T> &b, m3<T> &c) {
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      cx<T> acc = {0, 0};
+      acc = cmac_cj(acc, a.e[3 * i], b.e[3 * j]);
+      acc = cmac_cj(acc, a.e[3 * i + 1], b.e[3 * j + 1]);
+      acc = cmac_cj(acc, a.e[3 * i + 2], b.e[3 * j + 2]);
+      c.e[3 * i + j] = acc;
+    }
+}
+// Row 2 of an SU(3) matrix from rows 0 and 1: row2 = conj(row0 x row1).
+template <typename T> __device__ __forceinline__ void complete_row2(m3<T> &m) {
+  m.e[6] = cross_cj(m.e[1], m.e[5], m.e[2], m.e[4]);
+  m.e[7] = cross_cj(m.e[2], m.e[3], m.e[0], m.e[5]);
+  m.e[8] = cross_cj(m.e[0], m.e[4], m.e[1], m.e[3]);
+}
+
 // Projection to SU(3): normalise row 0; remove its component from row 1 and normalise;
 // row 2 = conj(row0 x row1), which has determinant +1.
 template <typename T> __device__ __forceinline__ void reunitarize(m3<T> &m) {

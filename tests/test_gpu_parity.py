@@ -10,7 +10,10 @@ from gpu_common import assert_matrix_close, theta_tol
 
 pytestmark = pytest.mark.gpu
 
-DIMS = [(4, 4, 4, 4), (8, 8, 8, 8), (6, 4, 8, 10), (3, 5, 4, 2), (12, 6, 5, 9), (2, 2, 2, 2)]
+# generic FFT passes: 4^4, 6x4x8x10, 3x5x4x2, 12x6x5x9, 2^4; specialised passes: 8^4, 16x16x24x8,
+# 24x24x8x48, 32x32x16x8
+DIMS = [(4, 4, 4, 4), (8, 8, 8, 8), (6, 4, 8, 10), (3, 5, 4, 2), (12, 6, 5, 9), (2, 2, 2, 2), (16, 16, 24, 8),
+        (24, 24, 8, 48), (32, 32, 16, 8)]
 
 
 @pytest.fixture(scope="module")
@@ -54,6 +57,22 @@ def test_fourier_filter(lgf, dims):
     assert_matrix_close(out, Dt_ref, scale=float(np.abs(Dt_ref).max()))
 
 
+@pytest.mark.parametrize("dims", [(8, 8, 8, 8), (16, 16, 24, 8), (24, 24, 8, 48)])
+def test_fourier_filter_generic_passes(lgf, dims, monkeypatch):
+    """The generic pass family on the shapes that normally take the specialised passes."""
+    monkeypatch.setenv("LGF_GENERIC_FFT", "1")
+    U = synth.config(dims, 25, 0.6)
+    D = oracle.delta(U)
+    Dt_ref = oracle.fourier_filter(D)
+    with lgf.Lattice(dims) as lat:
+        out = np.empty_like(D)
+        lat.filter(D, out)
+        out32 = np.empty_like(D)
+        lat.filter(D, out32, "fp32")
+    assert_matrix_close(out, Dt_ref, scale=float(np.abs(Dt_ref).max()))
+    assert_matrix_close(out32, Dt_ref, rtol=5e-6, scale=float(np.abs(Dt_ref).max()))
+
+
 @pytest.mark.parametrize("dims", DIMS)
 def test_gauge_field(lgf, dims):
     U = synth.config(dims, 23, 0.6)
@@ -76,7 +95,8 @@ def test_gauge_update(lgf, dims):
         assert_matrix_close(Ud.cpu().numpy(), U_ref)
 
 
-@pytest.mark.parametrize("dims,seed,eps", [((8, 8, 8, 8), 1, 0.3), ((6, 4, 8, 10), 5, 0.6), ((4, 4, 4, 8), 7, 0.6)])
+@pytest.mark.parametrize("dims,seed,eps", [((8, 8, 8, 8), 1, 0.3), ((6, 4, 8, 10), 5, 0.6), ((4, 4, 4, 8), 7, 0.6),
+                                           ((16, 16, 8, 8), 8, 0.6)])
 def test_trajectory_fp64(lgf, dims, seed, eps):
     """Whole fix: per-iteration theta and F histories, iteration count within +-1, final links."""
     U = synth.config(dims, seed, eps)
