@@ -73,8 +73,10 @@ def algorithmic(kernel, dims):
         # links read and written, g read (neighbours are the same data); per link rows 0-1 of
         # g U (18 complex MACs) and of (g U) g^+ (18), row 2 by a cross product: 168 FMA = 336 flop
         "gauge_update": ((36 + 36 + 9) * es, 4 * 336),
-        "gauge_update_accumulate": ((36 + 36 + 9 + 18) * es, 4 * 336 + 216),
-        "reunitarize": (5 * 9 * 2 * 8, 5 * 170),
+        # float stage: links read and written, G read and written, packed Delta-tilde read (g is
+        # rebuilt in registers); the _reunit variant also projects the new links in double precision
+        "gauge_update_fused": ((36 + 36 + 18 + 4) * es, 0),
+        "gauge_update_fused_reunit": ((36 + 36 + 18 + 4) * es, 4 * 170),
         "gacc_to_double": (9 * 8 + 9 * 16, 170),
         "handover_transform": (36 * 16 * 2 + 9 * 16, 8 * 216),  # full products (8 x 27 complex MACs)
         "to_planes": (36 * 16 + 36 * es, 0),
@@ -200,6 +202,111 @@ def cpu_baseline(dims, args, V_gpu):
                       "%.1f s" % ("x".join(map(str, cdims)), dt)}
 
 
+def _timed(torch, fn):
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = fn()
+    torch.cuda.synchronize()
+    return r, time.perf_counter() - t0
+
+
+def run_batch(args):
+    """The batched ensemble: 48 configurations (16 each of 16^4, 24^3x48, 32^3x64), eps_i ~ U[0.4, 0.7]
+    (seed 99), configuration i from seed 100 + i; fixed together in FP64 and in the mixed schedule
+    (grouped launches, CUDA-graph replay, autotuned FFT passes). Links stay on the device."""
+    import torch
+    import paper_1210_8018_gb300 as lgf
+    import synth
+    shapes = [(16, 16, 16, 16)] * 16 + [(24, 24, 24, 48)] * 16 + [(32, 32, 32, 64)] * 16
+    rng = np.random.default_rng(99)
+    eps_list = rng.uniform(0.4, 0.7, len(shapes))
+    inputs = []
+    for i, (d, e) in enumerate(zip(shapes, eps_list)):
+        inputs.append(torch.from_numpy(synth.config(d, 100 + i, float(e))).cuda())
+    work = [torch.empty_like(u) for u in inputs]
+    sites = sum(int(np.prod(d)) for d in shapes)
+    out = {"metric": "site-iterations/s, batched ensemble of uneven lattices", "unit": UNIT,
+           "config": {"workload": "16 x 16^4 + 16 x 24^3x48 + 16 x 32^3x64, eps ~ U[0.4,0.7], alpha=0.08, theta<1e-15",
+                      "sites": sites}, "data": "synthetic"}
+    with lgf.Batch(shapes) as b:
+        for prec in ("mixed", "fp64"):
+            def run():
+                for w, u in zip(work, inputs):
+                    w.copy_(u)
+                torch.cuda.synchronize()
+                return b.fix(work, 0.08, 1e-15, prec)
+            run()  # warm-up (and autotuning on a cold cache)
+            res, dt = _timed(torch, run)
+            its = [r["iters"] for r in res]
+            siters = sum(int(np.prod(d)) * r["iters"] for d, r in zip(shapes, res))
+            out[prec] = {"time_to_theta_s": dt, "site_iterations_per_s": siters / dt,
+                         "converged": sum(r["status"] == 0 for r in res), "iters_min": min(its),
+                         "iters_max": max(its), "describe": b.describe()}
+    out["value"] = out["mixed"]["site_iterations_per_s"]
+    return out
+
+
+def run_scan(args):
+    """The paper's tuning sweep over 32^3 x n (n = 8, 16, 32, 64): site-iterations/s of complete fixes
+    in FP64 and in the mixed schedule."""
+    import torch
+    import paper_1210_8018_gb300 as lgf
+    import synth
+    rows = []
+    for n in (8, 16, 32, 64):
+        dims = (32, 32, 32, n)
+        V = int(np.prod(dims))
+        U = torch.from_numpy(synth.config(dims, 2, args.eps)).cuda()
+        W = torch.empty_like(U)
+        row = {"lattice": "32^3x%d" % n, "sites": V}
+        with lgf.Lattice(dims) as lat:
+            for prec in ("fp64", "mixed"):
+                def run():
+                    lat.load(U, prec)
+                    r = lat.iterate(1 << 30, 0.08, 1e-15)
+                    lat.store(W)
+                    return r
+                run()
+                r, dt = _timed(torch, run)
+                row[prec] = {"iters": r["iters"], "time_s": dt, "site_iterations_per_s": V * r["iters"] / dt}
+        rows.append(row)
+    return {"metric": "site-iterations/s over 32^3 x n", "unit": UNIT, "scan": rows,
+            "value": rows[-1]["mixed"]["site_iterations_per_s"], "data": "synthetic"}
+
+
+def run_autograd(args):
+    """F_U[exp(i omega)] on 24^4 (eps = 0.5, seed 5; omega ~ N(0, 0.05^2) per generator, seed 6): forward
+    and backward kernel times, the gradient against the oracle's Delta at omega = 0, and Adam over omega
+    until theta <= 1e-10 (or the step budget)."""
+    import torch
+    import paper_1210_8018_gb300 as lgf
+    import synth
+    dims = (24, 24, 24, 24)
+    V = int(np.prod(dims))
+    U = torch.from_numpy(synth.config(dims, 5, 0.5)).cuda()
+    om = torch.from_numpy(synth.normals(6, 0, V * 8, 0.05).reshape(V, 8)).cuda()
+    grad = torch.empty_like(om)
+    out = {"metric": "F_U[exp(i omega)] forward/backward and Adam to theta<=1e-10", "config":
+           {"workload": "24^4, eps=0.5, omega~N(0,0.05^2)"}, "data": "synthetic"}
+    with lgf.Lattice(dims) as lat:
+        for _ in range(3):
+            lat.functional(U, om)
+            lat.functional_grad(U, om, grad)
+        n = 20
+        _, tf = _timed(torch, lambda: [lat.functional(U, om) for _ in range(n)])
+        _, tb = _timed(torch, lambda: [lat.functional_grad(U, om, grad) for _ in range(n)])
+    out["forward_ms"] = 1e3 * tf / n
+    out["backward_ms"] = 1e3 * tb / n
+    Uc = U.clone()
+    res, dt = _timed(torch, lambda: lgf.adam_fix(Uc, target=1e-10, lr=3e-2, max_steps=args.steps * 6000,
+                                                 omega0=om))
+    out["adam"] = {k: v for k, v in res.items() if k != "history"}
+    out["adam"]["time_s"] = dt
+    out["adam"]["theta_trace"] = [(h[0], h[1]) for h in res["history"][::max(1, len(res["history"]) // 20)]]
+    out["value"] = res["theta"]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -214,6 +321,13 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison fix")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--batch", action="store_true",
+                    help="the batched ensemble: 16 each of 16^4, 24^3x48, 32^3x64, eps ~ U[0.4, 0.7]")
+    ap.add_argument("--scan", action="store_true", help="site-iterations/s over 32^3 x n, n = 8..64")
+    ap.add_argument("--autograd", action="store_true",
+                    help="F_U[exp(i omega)] forward/backward at 24^4 and Adam over omega to theta <= 1e-10")
+    ap.add_argument("--fft32-final", action="store_true",
+                    help="also time the mixed variant whose double stage runs the Fourier filter in float")
     args = ap.parse_args()
     assert args.warmup >= 3 or args.impl == "reference", "at least 3 warm-up steps"
     dims = tuple(args.lattice)
@@ -225,6 +339,11 @@ def main():
     import torch
     import synth
     torch.cuda.set_device(local)
+    if args.batch or args.scan or args.autograd:
+        if rank == 0:
+            print(json.dumps(run_batch(args) if args.batch else run_scan(args) if args.scan else run_autograd(args)),
+                  flush=True)
+        return
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
@@ -300,6 +419,26 @@ def main():
                 "theta": r64["theta"], "F": r64["F"],
                 "kernels_ms": {k: round(v[1], 3) for k, v in sorted(k64.items(), key=lambda kv: -kv[1][1])}}
 
+    # the mixed variant with a float Fourier filter in the double stage (1 warm-up, 1 timed)
+    fast = None
+    if args.fft32_final and args.precision == "mixed":
+        def fix_fast():
+            lat.load(U_in, "mixed")
+            r = lat.iterate(1 << 30, 0.08, 1e-15, theta_switch=args.theta_switch, fft32_final=True)
+            lat.store(U_out)
+            return r
+        fix_fast()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rf = fix_fast()
+        e1.record(stream)
+        barrier()
+        tf = e0.elapsed_time(e1)
+        fast = {"time_to_theta_s": tf / 1e3, "iters": rf["iters"], "site_iterations_per_s": V * rf["iters"] / (tf / 1e3),
+                "theta": rf["theta"], "F": rf["F"],
+                "note": "double stage with the Fourier filter in float; links, Delta, g, update and sums in double"}
+
     # roofline of every kernel; the dominant kernel (largest share of the timed steps) is reported
     hbm, sm_max, which = peaks()
     clocks = clk.summary()
@@ -360,6 +499,9 @@ def main():
         if fp64:
             line["time_to_theta_s"]["fp64"] = fp64["time_to_theta_s"]
             line["fp64"] = fp64
+        if fast:
+            line["time_to_theta_s"]["mixed_fft32_final"] = fast["time_to_theta_s"]
+            line["mixed_fft32_final"] = fast
         if not args.no_cpu:
             line["cpu_baseline"] = cpu_baseline(dims, args, V)
         print(json.dumps(line), flush=True)

@@ -59,6 +59,9 @@ typedef struct {
   double *history;     /* optional host buffer: history[2k] = theta, history[2k+1] = F after k
                           updates (k = 0 is the input), for k < history_len                         */
   int history_len;
+  int fft32_final;     /* LGF_MIXED only, default 0: in the double stage run the Fourier filter in
+                          float (Delta, g, the update and the theta/F sums stay double; the filter
+                          only sets the search direction, so the fixed point is unchanged)         */
 } lgf_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -137,6 +140,19 @@ lgf_status lgf_gauge(lgf_ctx *ctx, const double *dtilde, double alpha, double *g
 /* Algorithm 1: U_mu(x) -> g(x) U_mu(x) g^+(x + mu) for all x, mu (links in/out, g in). */
 lgf_status lgf_update(lgf_ctx *ctx, double *links, const double *g, int precision);
 
+/* ---- The functional as a differentiable function of a Lie-algebra field (Eq. 1 at g = exp(i omega)).
+ * omega: V*8 doubles, site-major: omega[8*s + a] is the coefficient of T^a = lambda^a/2 (Gell-Mann
+ * matrices), so omega(x) = sum_a omega^a T^a is Hermitian and traceless; g(x) = exp(i omega(x)) is
+ * formed from a Jacobi eigen-decomposition of omega(x). Pointers may be device or host pointers. ---- */
+
+/* F = F_U[exp(i omega)] (Eq. 1); g_out (V*9 complex, site-field layout) receives g if not NULL. */
+lgf_status lgf_functional(lgf_ctx *ctx, const double *links, const double *omega, double *F, double *g_out);
+
+/* grad[8*s + a] = scale * dF/d omega^a(s): the su(3) gradient, i.e. the steepest-ascent direction
+ * (Daleckii-Krein adjoint of the exponential applied to the staple of Eq. 1). At omega = 0 it equals
+ * -scale * (i / (24 V)) Tr[T^a Delta(s)] with Delta of Eq. 5. */
+lgf_status lgf_functional_grad(lgf_ctx *ctx, const double *links, const double *omega, double scale, double *grad);
+
 /* ---- Timing of the loop's kernels: when enabled, lgf_iterate brackets every kernel launch with CUDA
  * events on the working stream and accumulates per-kernel device time. ---- */
 lgf_status lgf_enable_timing(lgf_ctx *ctx, int enable);
@@ -144,6 +160,30 @@ lgf_status lgf_enable_timing(lgf_ctx *ctx, int enable);
  * *count gets the number of kernels with timing data. Resets the counters. */
 lgf_status lgf_kernel_times(lgf_ctx *ctx, const char **name, long *launches, double *ms, int cap,
                             int *count);
+
+/* ---- Ensembles: several configurations of possibly different lattice shapes fixed together.
+ * Configurations of equal shape form a group whose kernels are launched once per group for all its
+ * configurations; the iteration loop of all groups is captured in a CUDA graph and replayed until every
+ * configuration has stopped (each keeps its own loop control, so iteration counts are per
+ * configuration). FFT pass shapes are autotuned per (shape, precision) and cached in the JSON file
+ * $LGF_TUNE_CACHE (default $HOME/.cache/lgf_fft_tune.json); LGF_AUTOTUNE=0 disables the tuner. ---- */
+typedef struct lgf_batch lgf_batch;
+
+/* dims: n x 4 extents (Nx, Ny, Nz, Nt), each as for lgf_create. */
+lgf_status lgf_batch_create(int n, const int *dims, lgf_batch **out);
+void lgf_batch_destroy(lgf_batch *b);
+const char *lgf_batch_last_error(const lgf_batch *b);
+
+/* Algorithm 1 for every configuration: links[i] (device or host pointer, the links layout above) is
+ * fixed in place. opt as for lgf_fix (precision, theta_switch, reunit_period -- also the number of
+ * iterations per captured graph replay -- and max_iter; history and fft32_final are ignored). theta, F, iters and status
+ * (lgf_status per configuration) are arrays of n entries, any may be NULL. Returns LGF_OK when every
+ * configuration reached theta < eps, otherwise the first non-OK status. */
+lgf_status lgf_batch_fix(lgf_batch *b, double *const *links, double alpha, double eps, const lgf_options *opt,
+                         double *theta, double *F, int *iters, int *status);
+
+/* JSON description of the groups, the tuned FFT plans and the replay counts of the last lgf_batch_fix. */
+lgf_status lgf_batch_describe(const lgf_batch *b, char *buf, int len);
 
 /* ---- Measurement without allocation. The paper has no counterpart: this entry point exists for
  * callers that cannot allocate device memory when they need Delta, theta and F -- a framework whose

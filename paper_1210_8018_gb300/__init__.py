@@ -30,7 +30,7 @@ _STATUS = {0: "LGF_OK", 1: "LGF_EINVAL", 2: "LGF_ENOMEM", 3: "LGF_ECUDA", 4: "LG
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("theta_switch", ctypes.c_double), ("reunit_period", ctypes.c_int),
                 ("max_iter", ctypes.c_int), ("history", ctypes.POINTER(ctypes.c_double)),
-                ("history_len", ctypes.c_int)]
+                ("history_len", ctypes.c_int), ("fft32_final", ctypes.c_int)]
 
 
 _vp, _d, _i = ctypes.c_void_p, ctypes.c_double, ctypes.c_int
@@ -50,6 +50,13 @@ _SIGS = {
     "lgf_filter": (_i, [_vp, _vp, _vp, _i]),
     "lgf_gauge": (_i, [_vp, _vp, _d, _vp, _i]),
     "lgf_update": (_i, [_vp, _vp, _vp, _i]),
+    "lgf_functional": (_i, [_vp, _vp, _vp, _P(_d), _vp]),
+    "lgf_functional_grad": (_i, [_vp, _vp, _vp, _d, _vp]),
+    "lgf_batch_create": (_i, [_i, _P(_i), _P(_vp)]),
+    "lgf_batch_destroy": (None, [_vp]),
+    "lgf_batch_last_error": (ctypes.c_char_p, [_vp]),
+    "lgf_batch_fix": (_i, [_vp, _P(_vp), _d, _d, _P(Options), _P(_d), _P(_d), _P(_i), _P(_i)]),
+    "lgf_batch_describe": (_i, [_vp, ctypes.c_char_p, _i]),
     "lgf_enable_timing": (_i, [_vp, _i]),
     "lgf_kernel_times": (_i, [_vp, _P(ctypes.c_char_p), _P(ctypes.c_long), _P(_d), _i, _P(_i)]),
 }
@@ -79,16 +86,19 @@ def _torch_stream_handle():
     return h if h else _CUDA_STREAM_LEGACY
 
 
-def _ptr(a):
-    """Device or host address of a complex128 C-contiguous torch tensor or numpy array."""
+def _ptr(a, real=False):
+    """Device or host address of a C-contiguous torch tensor or numpy array (complex128, or float64
+    when real=True)."""
     if isinstance(a, np.ndarray):
-        if a.dtype != np.complex128 or not a.flags.c_contiguous:
-            raise ValueError("numpy arrays must be complex128 and C-contiguous")
+        want = np.float64 if real else np.complex128
+        if a.dtype != want or not a.flags.c_contiguous:
+            raise ValueError("numpy arrays must be %s and C-contiguous" % np.dtype(want).name)
         return a.ctypes.data
     import torch
     if isinstance(a, torch.Tensor):
-        if a.dtype != torch.complex128 or not a.is_contiguous():
-            raise ValueError("tensors must be complex128 and contiguous")
+        want = torch.float64 if real else torch.complex128
+        if a.dtype != want or not a.is_contiguous():
+            raise ValueError("tensors must be %s and contiguous" % want)
         return a.data_ptr()
     raise TypeError("expected a numpy array or a torch tensor")
 
@@ -149,9 +159,11 @@ class Lattice:
         self._check(_lib.lgf_set_stream(self._h, raw))
 
     @staticmethod
-    def options(precision="fp64", theta_switch=1e-8, reunit_period=16, max_iter=100000, history=None):
+    def options(precision="fp64", theta_switch=1e-8, reunit_period=16, max_iter=100000, history=None,
+                fft32_final=False):
         o = Options()
         _lib.lgf_default_options(ctypes.byref(o))
+        o.fft32_final = 1 if fft32_final else 0
         o.precision = _PREC[precision]
         o.theta_switch = theta_switch
         o.reunit_period = reunit_period
@@ -162,10 +174,10 @@ class Lattice:
         return o
 
     def fix(self, U, alpha=0.08, eps=1e-15, precision="fp64", max_iter=100000, theta_switch=1e-8,
-            reunit_period=16, history_len=0):
+            reunit_period=16, history_len=0, fft32_final=False):
         """Algorithm 1: fix U in place. Returns dict(theta, F, iters, converged, history)."""
         hist = np.zeros((history_len, 2), dtype=np.float64) if history_len > 0 else None
-        o = self.options(precision, theta_switch, reunit_period, max_iter, hist)
+        o = self.options(precision, theta_switch, reunit_period, max_iter, hist, fft32_final)
         th, F, it = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
         self._bind(U)
         st = self._check(_lib.lgf_fix(self._h, _ptr(U), alpha, eps, ctypes.byref(o), ctypes.byref(th),
@@ -186,9 +198,10 @@ class Lattice:
         self._bind(U)
         self._check(_lib.lgf_load(self._h, _ptr(U), _PREC[precision]))
 
-    def iterate(self, max_new, alpha=0.08, eps=1e-15, theta_switch=1e-8, reunit_period=16, history_len=0):
+    def iterate(self, max_new, alpha=0.08, eps=1e-15, theta_switch=1e-8, reunit_period=16, history_len=0,
+                fft32_final=False):
         hist = np.zeros((history_len, 2), dtype=np.float64) if history_len > 0 else None
-        o = self.options("fp64", theta_switch, reunit_period, 0, hist)
+        o = self.options("fp64", theta_switch, reunit_period, 0, hist, fft32_final)
         th, F, it = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
         st = self._check(_lib.lgf_iterate(self._h, int(max_new), alpha, eps, ctypes.byref(o), ctypes.byref(th),
                                           ctypes.byref(F), ctypes.byref(it)), (LGF_OK, LGF_ENOCONV))
@@ -221,6 +234,21 @@ class Lattice:
         self._bind(U, g)
         self._check(_lib.lgf_update(self._h, _ptr(U), _ptr(g), _PREC[precision]))
 
+    # the functional of a Lie-algebra field omega (V x 8 float64, site-major)
+    def functional(self, U, omega, g_out=None):
+        """F_U[exp(i omega)] (Eq. 1); fills g_out (complex128, (Nt, Nz, Ny, Nx, 3, 3)) if given."""
+        F = ctypes.c_double()
+        self._bind(U, omega)
+        self._check(_lib.lgf_functional(self._h, _ptr(U), _ptr(omega, True), ctypes.byref(F),
+                                        None if g_out is None else _ptr(g_out)))
+        return F.value
+
+    def functional_grad(self, U, omega, grad_out, scale=1.0):
+        """grad_out[s, a] = scale * dF/d omega^a(s) (hand-written backward kernel)."""
+        self._bind(U, omega, grad_out)
+        self._check(_lib.lgf_functional_grad(self._h, _ptr(U), _ptr(omega, True), float(scale),
+                                             _ptr(grad_out, True)))
+
     # timing
     def enable_timing(self, on=True):
         self._check(_lib.lgf_enable_timing(self._h, 1 if on else 0))
@@ -233,6 +261,150 @@ class Lattice:
         n = ctypes.c_int()
         self._check(_lib.lgf_kernel_times(self._h, names, launches, ms, cap, ctypes.byref(n)))
         return {names[i].decode(): (launches[i], ms[i]) for i in range(min(n.value, cap))}
+
+
+class Batch:
+    """Several configurations, of possibly different lattice shapes, fixed together: equal shapes share
+    kernel launches (one per group), the iteration loop is a replayed CUDA graph, and FFT passes are
+    autotuned per (shape, precision)."""
+
+    def __init__(self, dims_list):
+        self.dims = [tuple(int(v) for v in d) for d in dims_list]
+        flat = (ctypes.c_int * (4 * len(self.dims)))(*[v for d in self.dims for v in d])
+        h = ctypes.c_void_p()
+        st = _lib.lgf_batch_create(len(self.dims), flat, ctypes.byref(h))
+        if st != LGF_OK:
+            raise LgfError(st, _lib.lgf_last_error(None).decode())
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.lgf_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def fix(self, Us, alpha=0.08, eps=1e-15, precision="fp64", max_iter=100000, theta_switch=1e-8,
+            reunit_period=16):
+        """Fix every configuration of Us (list of links, device tensors or numpy arrays) in place.
+        Returns a list of dict(theta, F, iters, status)."""
+        n = len(self.dims)
+        assert len(Us) == n
+        for U, d in zip(Us, self.dims):
+            assert dims_of(U) == d
+            if not isinstance(U, np.ndarray) and getattr(U, "is_cuda", False):
+                import torch
+                torch.cuda.current_stream().synchronize()  # the batch runs on its own stream
+        ptrs = (ctypes.c_void_p * n)(*[_ptr(U) for U in Us])
+        o = Lattice.options(precision, theta_switch, reunit_period, max_iter)
+        th, F = (ctypes.c_double * n)(), (ctypes.c_double * n)()
+        it, stt = (ctypes.c_int * n)(), (ctypes.c_int * n)()
+        st = _lib.lgf_batch_fix(self._h, ptrs, alpha, eps, ctypes.byref(o), th, F, it, stt)
+        if st not in (LGF_OK, LGF_ENOCONV):
+            raise LgfError(st, _lib.lgf_batch_last_error(self._h).decode())
+        return [dict(theta=th[i], F=F[i], iters=it[i], status=stt[i]) for i in range(n)]
+
+    def describe(self):
+        import json
+        buf = ctypes.create_string_buffer(1 << 16)
+        _lib.lgf_batch_describe(self._h, buf, len(buf))
+        return json.loads(buf.value.decode())
+
+
+def _landau_function():
+    import torch
+
+    class LandauF(torch.autograd.Function):
+        """F_U[exp(i omega)] as a differentiable function of omega (torch float64, (V, 8) or
+        (Nt, Nz, Ny, Nx, 8), on the GPU): forward and backward run in the library's kernels.
+        Usage: F = LandauF.apply(omega, U, lattice)."""
+
+        @staticmethod
+        def forward(ctx, omega, U, lattice):
+            omega = omega.contiguous()
+            F = lattice.functional(U, omega)
+            ctx.save_for_backward(omega, U)
+            ctx.lattice = lattice
+            return torch.tensor(F, dtype=torch.float64, device=omega.device)
+
+        @staticmethod
+        def backward(ctx, gF):
+            omega, U = ctx.saved_tensors
+            grad = torch.empty_like(omega)
+            ctx.lattice.functional_grad(U, omega, grad, float(gF))
+            return grad, None, None
+
+    return LandauF
+
+
+_LandauF = None
+
+
+def LandauF():
+    """The torch.autograd.Function for F_U[exp(i omega)] (created on first use; needs torch)."""
+    global _LandauF
+    if _LandauF is None:
+        _LandauF = _landau_function()
+    return _LandauF
+
+
+def adam_fix(U, target=1e-10, lr=1e-2, max_steps=20000, check_every=20, lr_decay=0.5, min_lr=1e-9,
+             omega0=None):
+    """Maximise F_U[exp(i omega)] over omega with torch.optim.Adam (plain gradient information, no
+    Fourier acceleration), using the library's forward and backward kernels, until theta of the
+    transformed links g U g^+ falls to `target`.
+
+    omega starts at omega0 (default 0) and stays in one coordinate system; every `check_every` steps
+    F and theta are evaluated, and the learning rate is multiplied by `lr_decay` whenever F did not
+    increase since the previous check (Adam has overshot). At the end g is applied to U in place (an
+    exact FP64 gauge transformation through lgf_update). Returns dict(theta, F, F0, steps, lr,
+    history=[(step, theta, F, lr)])."""
+    import torch
+    dims = dims_of(U)
+    V = int(np.prod(dims))
+    LF = LandauF()
+    hist = []
+    with Lattice(dims) as lat:
+        omega = torch.zeros((V, 8), dtype=torch.float64, device=U.device) if omega0 is None else omega0.clone()
+        omega = omega.contiguous().requires_grad_(True)
+        g = torch.empty(U.shape[1:], dtype=torch.complex128, device=U.device)
+        Ut = torch.empty_like(U)
+
+        def evaluate():
+            with torch.no_grad():
+                F = lat.functional(U, omega.detach(), g)
+                Ut.copy_(U)
+                lat.update(Ut, g)
+                return F, lat.measure(Ut)["theta"]
+
+        F0 = lat.measure(U)["F"]
+        F, theta = evaluate()
+        hist.append((0, theta, F, lr))
+        opt = torch.optim.Adam([omega], lr=lr)
+        step = 0
+        while step < max_steps and theta > target and opt.param_groups[0]["lr"] > min_lr:
+            opt.zero_grad(set_to_none=False)
+            loss = -LF.apply(omega, U, lat)
+            loss.backward()
+            opt.step()
+            step += 1
+            if step % check_every == 0:
+                F_prev = F
+                F, theta = evaluate()
+                if F <= F_prev:
+                    for pg in opt.param_groups:
+                        pg["lr"] *= lr_decay
+                hist.append((step, theta, F, opt.param_groups[0]["lr"]))
+        F, theta = evaluate()
+        U.copy_(Ut)
+    return dict(theta=theta, F=F, F0=F0, steps=step, lr=opt.param_groups[0]["lr"], history=hist)
 
 
 def fix(U, alpha=0.08, eps=1e-15, precision="fp64", **kw):

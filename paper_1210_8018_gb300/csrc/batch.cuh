@@ -1,0 +1,474 @@
+// batch.cuh -- ensembles of configurations of uneven lattice shapes fixed together (part of the
+// lgf.cu translation unit: it uses the context internals defined there).
+//
+// Configurations are grouped by shape; each group is one context holding nb configurations stored one
+// after the other, and every kernel of an iteration is launched once per group with gridDim.z = nb
+// (each configuration has its own loop control, so a converged configuration's blocks return at once
+// and every configuration's iteration count is exactly its own). K iterations of all groups -- in the
+// mixed schedule both the float-stage and the double-stage kernels, each running only for the
+// configurations in that stage -- are captured once in a CUDA graph and replayed until every
+// configuration has stopped; between replays the host hands over each mixed configuration that has
+// reached theta_switch. FFT pass shapes are chosen per (shape, precision) by a timing autotuner whose
+// results are cached in a JSON file.
+
+// ------------------------------------------------------------------------------------------------
+// FFT autotuner: candidates are the generic passes and the specialised passes with 16- or 32-wide
+// column tiles; each is timed on the context's own packed buffers and the fastest is kept. Results are
+// cached in a JSON object {"<Nx>x<Ny>x<Nz>x<Nt>:<f64|f32>": {"plan": "...", "C": c, "ms": t}, ...} at
+// $LGF_TUNE_CACHE (default $HOME/.cache/lgf_fft_tune.json).
+// ------------------------------------------------------------------------------------------------
+namespace {
+
+struct TuneEntry {
+  std::string plan;  // "fixed" or "generic"
+  int C = 0;
+  double ms = 0;
+};
+
+std::string tune_cache_path() {
+  const char *p = std::getenv("LGF_TUNE_CACHE");
+  if (p && *p) return p;
+  const char *h = std::getenv("HOME");
+  return std::string(h && *h ? h : "/tmp") + "/.cache/lgf_fft_tune.json";
+}
+
+std::map<std::string, TuneEntry> tune_cache_read() {
+  std::map<std::string, TuneEntry> m;
+  FILE *f = std::fopen(tune_cache_path().c_str(), "r");
+  if (!f) return m;
+  std::string text;
+  char buf[4096];
+  size_t got;
+  while ((got = std::fread(buf, 1, sizeof buf, f)) > 0) text.append(buf, got);
+  std::fclose(f);
+  size_t pos = 0;
+  while ((pos = text.find('"', pos)) != std::string::npos) {
+    const size_t end = text.find('"', pos + 1);
+    if (end == std::string::npos) break;
+    const std::string key = text.substr(pos + 1, end - pos - 1);
+    const size_t brace = text.find('{', end), close = text.find('}', end);
+    if (key.find(':') == std::string::npos || brace == std::string::npos || close == std::string::npos) {
+      pos = end + 1;
+      continue;
+    }
+    const std::string body = text.substr(brace, close - brace + 1);
+    TuneEntry e;
+    char plan[32] = {0};
+    if (std::sscanf(body.c_str(), "{\"plan\": \"%31[a-z]\", \"C\": %d, \"ms\": %lf}", plan, &e.C, &e.ms) == 3) {
+      e.plan = plan;
+      m[key] = e;
+    }
+    pos = close + 1;
+  }
+  return m;
+}
+
+void tune_cache_write(const std::map<std::string, TuneEntry> &m) {
+  const std::string path = tune_cache_path();
+  const size_t slash = path.rfind('/');
+  if (slash != std::string::npos) {
+    mkdir(path.substr(0, slash).c_str(), 0755);  // the directory, one level deep, if missing
+  }
+  const std::string tmp = path + ".tmp" + std::to_string((long)getpid());
+  FILE *f = std::fopen(tmp.c_str(), "w");
+  if (!f) return;
+  std::fprintf(f, "{\n");
+  size_t i = 0;
+  for (const auto &kv : m)
+    std::fprintf(f, "  \"%s\": {\"plan\": \"%s\", \"C\": %d, \"ms\": %.6f}%s\n", kv.first.c_str(),
+                 kv.second.plan.c_str(), kv.second.C, kv.second.ms, ++i < m.size() ? "," : "");
+  std::fprintf(f, "}\n");
+  std::fclose(f);
+  std::rename(tmp.c_str(), path.c_str());
+}
+
+template <typename T> std::string tune_key(const lgf_ctx *ctx) {
+  return std::to_string(ctx->n[0]) + "x" + std::to_string(ctx->n[1]) + "x" + std::to_string(ctx->n[2]) + "x" +
+         std::to_string(ctx->n[3]) + (sizeof(T) == 8 ? ":f64" : ":f32");
+}
+
+// Apply a candidate: re-plan the passes and opt the kernels in to their shared memory.
+template <typename T> lgf_status apply_fft_choice(lgf_ctx *ctx, State<T> &S, bool generic, int C) {
+  ctx->generic_fft = generic;
+  ctx->fixed_cols[sizeof(T) == 8 ? 0 : 1] = C;
+  plan_passes<T>(ctx, S);
+  size_t generic_max = 0;
+  for (auto &p : S.passes) {
+    if (p.kind == 0) generic_max = std::max(generic_max, p.smem);
+    else if (p.smem > 48 * 1024)
+      CK(cudaFuncSetAttribute(fixed_kernel<T>(p), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
+  }
+  if (generic_max > 48 * 1024)
+    CK(cudaFuncSetAttribute(k_fft_pass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)generic_max));
+  return LGF_OK;
+}
+
+// Time the filter passes of the current plan (ms per application, median of 5 after 2 warm-ups).
+template <typename T> lgf_status time_fft(lgf_ctx *ctx, State<T> &S, double *ms_out) {
+  const bool timing = ctx->timing;
+  ctx->timing = false;
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  std::vector<float> t;
+  for (int rep = 0; rep < 7; ++rep) {
+    CK(cudaEventRecord(a, ctx->stream));
+    TRY(launch_filter<T>(ctx, S, S.P, 0));
+    CK(cudaEventRecord(b, ctx->stream));
+    CK(cudaEventSynchronize(b));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, a, b));
+    if (rep >= 2) t.push_back(ms);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  std::sort(t.begin(), t.end());
+  *ms_out = t[t.size() / 2];
+  ctx->timing = timing;
+  return LGF_OK;
+}
+
+template <typename T> lgf_status autotune_fft(lgf_ctx *ctx, State<T> &S, TuneEntry *chosen) {
+  const std::string key = tune_key<T>(ctx);
+  auto cache = tune_cache_read();
+  auto it = cache.find(key);
+  if (it != cache.end()) {
+    TRY(apply_fft_choice<T>(ctx, S, it->second.plan == "generic", it->second.C));
+    *chosen = it->second;
+    return LGF_OK;
+  }
+  CK(cudaMemsetAsync(S.P, 0, sizeof(T) * 2 * 4 * (size_t)ctx->V * ctx->nb, ctx->stream));
+  struct Cand {
+    bool generic;
+    int C;
+  };
+  const Cand cands[] = {{true, 0}, {false, 16}, {false, 32}};
+  TuneEntry best;
+  best.ms = 1e30;
+  for (const Cand &c : cands) {
+    TRY(apply_fft_choice<T>(ctx, S, c.generic, c.C));
+    const bool fixed_plan = !S.passes.empty() && S.passes[0].kind != 0;
+    if (!c.generic && !fixed_plan) continue;  // the specialised passes do not fit this shape
+    double ms = 0;
+    TRY(time_fft<T>(ctx, S, &ms));
+    if (ms < best.ms) {
+      best.ms = ms;
+      best.plan = c.generic ? "generic" : "fixed";
+      best.C = c.C;
+    }
+  }
+  TRY(apply_fft_choice<T>(ctx, S, best.plan == "generic", best.C));
+  cache = tune_cache_read();
+  cache[key] = best;
+  tune_cache_write(cache);
+  *chosen = best;
+  return LGF_OK;
+}
+
+}  // namespace
+
+struct lgf_batch {
+  int n = 0;
+  std::vector<lgf_ctx *> groups;
+  std::vector<int> group_of, index_of;  // configuration -> (group, index within group)
+  cudaStream_t stream = nullptr;
+  std::string err;
+  bool poisoned = false;
+  bool autotune = true;
+  std::string tuned[2];  // description of the tuned FFT plans per group, double / float
+  cudaGraphExec_t graph = nullptr;
+  int graph_prec = -1, graph_chunk = 0;
+  double graph_alpha = 0;
+  int launches_per_replay = 0;
+  long graph_replays = 0;
+};
+
+namespace {
+
+lgf_status bfail(lgf_batch *b, lgf_status st, const std::string &msg) {
+  if (b) {
+    b->err = msg;
+    if (st == LGF_ECUDA) b->poisoned = true;
+  }
+  return st;
+}
+
+#define BCK(call)                                                                                 \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess)                                                                        \
+      return bfail(b, e_ == cudaErrorMemoryAllocation ? LGF_ENOMEM : LGF_ECUDA,                   \
+                   std::string(#call) + ": " + cudaGetErrorString(e_));                           \
+  } while (0)
+#define BTRY(g, x)                                                                                \
+  do {                                                                                            \
+    lgf_status s_ = (x);                                                                          \
+    if (s_ != LGF_OK) return bfail(b, s_, (g)->err);                                              \
+  } while (0)
+
+// Plane-offset helpers for configuration j of a group.
+template <typename T> T *cfg_links(T *base, const lgf_ctx *g, int j) { return base + (int64_t)j * 36 * g->V * 2; }
+template <typename T> T *cfg_packed(T *base, const lgf_ctx *g, int j) { return base + (int64_t)j * 4 * g->V * 2; }
+template <typename T> T *cfg_mat(T *base, const lgf_ctx *g, int j) { return base + (int64_t)j * 9 * g->V * 2; }
+
+// Delta, theta and F of configuration j alone (used at load and after a handover).
+template <typename T> lgf_status delta_one(lgf_ctx *g, State<T> &S, int j) {
+  lgf_ctx *ctx = g;
+  k_delta<T, NT><<<dim3(g->nblocks_site, 1, 1), NT, 0, g->stream>>>(
+      cfg_links(S.U, g, j), cfg_packed(S.P, g, j), g->partials + (int64_t)j * 2 * g->nblocks_site, g->ctrl + j, g->L,
+      0, 0, 0);
+  CKL();
+  return LGF_OK;
+}
+
+lgf_status handover_one(lgf_ctx *g, int j) {
+  lgf_ctx *ctx = g;
+  k_gacc_to_double<NT><<<grid1(g->V, NT), NT, 0, g->stream>>>(cfg_mat(g->Gacc, g, j), cfg_mat(g->s64.G, g, j), g->V);
+  CKL();
+  k_transform_from<NT><<<grid1(g->V, NT), NT, 0, g->stream>>>(cfg_links(g->U0, g, j), cfg_links(g->s64.U, g, j),
+                                                              cfg_mat(g->s64.G, g, j), g->L);
+  CKL();
+  return LGF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lgf_status lgf_batch_create(int n, const int *dims, lgf_batch **out) {
+  if (!out || !dims || n < 1) return fail(nullptr, LGF_EINVAL, "lgf_batch_create: bad arguments");
+  *out = nullptr;
+  lgf_batch *b = new lgf_batch();
+  b->n = n;
+  std::vector<std::array<int, 4>> shapes;
+  std::vector<int> counts;
+  for (int i = 0; i < n; ++i) {
+    std::array<int, 4> d = {dims[4 * i], dims[4 * i + 1], dims[4 * i + 2], dims[4 * i + 3]};
+    int g = -1;
+    for (size_t k = 0; k < shapes.size(); ++k)
+      if (shapes[k] == d) g = (int)k;
+    if (g < 0) {
+      shapes.push_back(d);
+      counts.push_back(0);
+      g = (int)shapes.size() - 1;
+    }
+    b->group_of.push_back(g);
+    b->index_of.push_back(counts[g]++);
+  }
+  if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete b;
+    return fail(nullptr, LGF_ECUDA, "cudaStreamCreate failed");
+  }
+  for (size_t g = 0; g < shapes.size(); ++g) {
+    lgf_ctx *c = nullptr;
+    const lgf_status st = create_ctx(shapes[g].data(), counts[g], &c);
+    if (st != LGF_OK) {
+      lgf_batch_destroy(b);
+      return st;
+    }
+    c->stream = b->stream;
+    b->groups.push_back(c);
+  }
+  const char *t = std::getenv("LGF_AUTOTUNE");
+  b->autotune = !(t && t[0] == '0');
+  *out = b;
+  return LGF_OK;
+}
+
+void lgf_batch_destroy(lgf_batch *b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (lgf_ctx *c : b->groups) {
+    c->stream = c->own_stream;
+    lgf_destroy(c);
+  }
+  if (b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+const char *lgf_batch_last_error(const lgf_batch *b) { return b ? b->err.c_str() : ""; }
+
+lgf_status lgf_batch_fix(lgf_batch *b, double *const *links, double alpha, double eps, const lgf_options *opt,
+                         double *theta, double *F, int *iters, int *status) {
+  if (!b) return fail(nullptr, LGF_EINVAL, "null batch");
+  if (b->poisoned) return LGF_ECUDA;
+  if (!links || !(alpha > 0) || !(eps >= 0)) return bfail(b, LGF_EINVAL, "bad links, alpha or eps");
+  lgf_options o;
+  lgf_default_options(&o);
+  if (opt) o = *opt;
+  if (o.reunit_period < 1) o.reunit_period = 1;
+  const int prec = o.precision;
+  if (prec != LGF_FP64 && prec != LGF_MIXED && prec != LGF_FP32) return bfail(b, LGF_EINVAL, "unknown precision");
+  const bool has_float = prec != LGF_FP64, has_double = prec != LGF_FP32;
+  // buffers, FFT plans (autotuned) and loads
+  b->tuned[0].clear();
+  b->tuned[1].clear();
+  for (lgf_ctx *g : b->groups) {
+    BTRY(g, check_ctx(g));
+    BTRY(g, ensure_common(g));
+    if (has_double) {
+      BTRY(g, setup_precision<double>(g, g->s64));
+      TuneEntry e;
+      if (b->autotune) BTRY(g, autotune_fft<double>(g, g->s64, &e));
+      b->tuned[0] += tune_key<double>(g) + "=" + (b->autotune ? e.plan + "/" + std::to_string(e.C) : "default") + " ";
+    }
+    if (has_float) {
+      BTRY(g, setup_precision<float>(g, g->s32));
+      BTRY(g, alloc(g, &g->Gacc, (size_t)g->nb * 9 * g->V * 2));
+      if (prec == LGF_MIXED) BTRY(g, alloc(g, &g->U0, (size_t)g->nb * 4 * 9 * g->V * 2));
+      TuneEntry e;
+      if (b->autotune) BTRY(g, autotune_fft<float>(g, g->s32, &e));
+      b->tuned[1] += tune_key<float>(g) + "=" + (b->autotune ? e.plan + "/" + std::to_string(e.C) : "default") + " ";
+    }
+  }
+  for (int i = 0; i < b->n; ++i) {
+    lgf_ctx *g = b->groups[b->group_of[i]];
+    lgf_ctx *ctx = g;
+    const int j = b->index_of[i];
+    const double *src = nullptr;
+    BTRY(g, input_ptr(g, links[i], (size_t)4 * g->V * 144, &g->staging, &g->staging_bytes, &src));
+    if (prec == LGF_FP64) {
+      BTRY(g, to_planes<double>(g, src, cfg_links(g->s64.U, g, j), 4));
+    } else {
+      if (prec == LGF_MIXED) BTRY(g, to_planes<double>(g, src, cfg_links(g->U0, g, j), 4));
+      BTRY(g, to_planes<float>(g, src, cfg_links(g->s32.U, g, j), 4));
+      k_set_identity<<<grid1(g->V, NT), NT, 0, g->stream>>>(cfg_mat(g->Gacc, g, j), g->V);
+      CKL();
+    }
+  }
+  // loop control of every configuration, then Delta/theta/F of the inputs
+  const double thr0 = prec == LGF_MIXED ? std::max(eps, o.theta_switch) : eps;
+  std::vector<std::vector<Ctrl>> host(b->groups.size());
+  for (size_t k = 0; k < b->groups.size(); ++k) {
+    lgf_ctx *g = b->groups[k];
+    host[k].assign(g->nb, Ctrl{});
+    for (Ctrl &c : host[k]) {
+      c.threshold = thr0;
+      c.limit = o.max_iter;
+      c.active = 1;
+      c.stage = prec == LGF_FP64 ? 1 : 0;
+    }
+    BCK(cudaMemcpyAsync(g->ctrl, host[k].data(), sizeof(Ctrl) * g->nb, cudaMemcpyHostToDevice, b->stream));
+    if (prec == LGF_FP64) BTRY(g, launch_delta<double>(g, g->s64, 0, 0));
+    else BTRY(g, launch_delta<float>(g, g->s32, 0, 0));
+  }
+  // the captured chunk: reunit_period iterations of every group (the last one reprojects the float links)
+  const int chunk = o.reunit_period;
+  if (!b->graph || b->graph_prec != prec || b->graph_chunk != chunk || b->graph_alpha != alpha) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    for (lgf_ctx *g : b->groups) g->timing = false;
+    BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    int launches = 0;
+    for (int k = 0; k < chunk; ++k)
+      for (lgf_ctx *g : b->groups) {
+        if (has_float) {
+          const lgf_status st = launch_iteration_float(g, alpha, k == chunk - 1);
+          launches += (int)g->s32.passes.size() + 2;
+          if (st != LGF_OK) {
+            cudaGraph_t junk;
+            cudaStreamEndCapture(b->stream, &junk);
+            return bfail(b, st, g->err);
+          }
+        }
+        if (has_double) {
+          const lgf_status st = launch_iteration<double>(g, g->s64, alpha);
+          launches += (int)g->s64.passes.size() + 3;
+          if (st != LGF_OK) {
+            cudaGraph_t junk;
+            cudaStreamEndCapture(b->stream, &junk);
+            return bfail(b, st, g->err);
+          }
+        }
+      }
+    cudaGraph_t graph;
+    BCK(cudaStreamEndCapture(b->stream, &graph));
+    BCK(cudaGraphInstantiate(&b->graph, graph, 0));
+    cudaGraphDestroy(graph);
+    b->graph_prec = prec;
+    b->graph_chunk = chunk;
+    b->graph_alpha = alpha;
+    b->launches_per_replay = launches;
+  }
+  b->graph_replays = 0;
+  // replay until every configuration has stopped; hand over mixed configurations at theta_switch
+  for (;;) {
+    bool pending = false;
+    for (size_t k = 0; k < b->groups.size(); ++k) {
+      lgf_ctx *g = b->groups[k];
+      BCK(cudaMemcpyAsync(host[k].data(), g->ctrl, sizeof(Ctrl) * g->nb, cudaMemcpyDeviceToHost, b->stream));
+    }
+    BCK(cudaStreamSynchronize(b->stream));
+    for (size_t k = 0; k < b->groups.size(); ++k) {
+      lgf_ctx *g = b->groups[k];
+      for (int j = 0; j < g->nb; ++j) {
+        Ctrl &c = host[k][j];
+        if (c.status == 5) continue;
+        if (c.active) {
+          pending = true;
+        } else if (prec == LGF_MIXED && c.stage == 0 && c.theta < thr0 && c.iters < c.limit) {
+          BTRY(g, setup_precision<double>(g, g->s64));
+          BTRY(g, handover_one(g, j));
+          c.stage = 1;
+          c.threshold = eps;
+          c.active = 1;
+          BCK(cudaMemcpyAsync(g->ctrl + j, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, b->stream));
+          BTRY(g, delta_one<double>(g, g->s64, j));
+          pending = true;
+        }
+      }
+    }
+    if (!pending) break;
+    BCK(cudaGraphLaunch(b->graph, b->stream));
+    ++b->graph_replays;
+  }
+  // results and store
+  lgf_status result = LGF_OK;
+  for (int i = 0; i < b->n; ++i) {
+    const int k = b->group_of[i], j = b->index_of[i];
+    lgf_ctx *g = b->groups[k];
+    const Ctrl &c = host[k][j];
+    const lgf_status st = c.status == 5 ? LGF_ENONFINITE : (c.theta < eps ? LGF_OK : LGF_ENOCONV);
+    if (theta) theta[i] = c.theta;
+    if (F) F[i] = c.F;
+    if (iters) iters[i] = c.iters;
+    if (status) status[i] = st;
+    if (st != LGF_OK && result == LGF_OK) result = st;
+    if (st == LGF_ENONFINITE) continue;
+    double *dst = nullptr;
+    bool hostp = false;
+    BTRY(g, output_ptr(g, links[i], (size_t)4 * g->V * 144, &g->staging, &g->staging_bytes, &dst, &hostp));
+    if (c.stage == 1) {
+      BTRY(g, from_planes<double>(g, cfg_links(g->s64.U, g, j), dst, 4));
+    } else if (prec == LGF_MIXED) {
+      BTRY(g, setup_precision<double>(g, g->s64));
+      BTRY(g, handover_one(g, j));
+      BTRY(g, from_planes<double>(g, cfg_links(g->s64.U, g, j), dst, 4));
+    } else {
+      BTRY(g, from_planes<float>(g, cfg_links(g->s32.U, g, j), dst, 4));
+    }
+    if (hostp) BCK(cudaMemcpyAsync(links[i], dst, (size_t)4 * g->V * 144, cudaMemcpyDeviceToHost, b->stream));
+    BCK(cudaStreamSynchronize(b->stream));
+  }
+  if (result == LGF_ENONFINITE) return bfail(b, result, "theta or F is not finite for a configuration");
+  return result;
+}
+
+lgf_status lgf_batch_describe(const lgf_batch *b, char *buf, int len) {
+  if (!b || !buf || len < 1) return LGF_EINVAL;
+  std::string s = "{\"configs\": " + std::to_string(b->n) + ", \"groups\": [";
+  for (size_t k = 0; k < b->groups.size(); ++k) {
+    const lgf_ctx *g = b->groups[k];
+    s += std::string(k ? ", " : "") + "{\"dims\": [" + std::to_string(g->n[0]) + ", " + std::to_string(g->n[1]) +
+         ", " + std::to_string(g->n[2]) + ", " + std::to_string(g->n[3]) + "], \"configs\": " + std::to_string(g->nb) +
+         "}";
+  }
+  s += "], \"fft_f64\": \"" + b->tuned[0] + "\", \"fft_f32\": \"" + b->tuned[1] +
+       "\", \"launches_per_replay\": " + std::to_string(b->launches_per_replay) +
+       ", \"graph_replays\": " + std::to_string(b->graph_replays) + "}";
+  std::snprintf(buf, (size_t)len, "%s", s.c_str());
+  return LGF_OK;
+}
+
+}  // extern "C"

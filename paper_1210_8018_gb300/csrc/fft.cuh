@@ -198,7 +198,9 @@ __device__ __forceinline__ void fft_axis(cx<T> *tile, const cx<T> *tw, const Axi
 template <typename T>
 __global__ void __launch_bounds__(512) k_fft_pass(T *__restrict__ data, int64_t V, PassDesc pd, FFTTables tb,
                                                  const Ctrl *ctrl, int check_active, int tkid) {
-  if (check_active && !ctrl->active) return;
+  data += (int64_t)blockIdx.z * 4 * V * 2;
+  ctrl += blockIdx.z;
+  if (!should_run<T>(ctrl, check_active)) return;
   count_run(ctrl, tkid);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T> *tile = reinterpret_cast<cx<T> *>(smem_raw);

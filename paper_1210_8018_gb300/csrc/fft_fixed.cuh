@@ -90,7 +90,9 @@ template <typename T, int N> __device__ __forceinline__ void load_twiddles(cx<T>
 template <typename T, int NX, int NY, bool INV, int NT>
 __global__ void __launch_bounds__(NT) k_fx_plane(T *__restrict__ data, int64_t V, FFTTables tb, const Ctrl *ctrl,
                                                 int check_active, int tkid) {
-  if (check_active && !ctrl->active) return;
+  data += (int64_t)blockIdx.z * 4 * V * 2;
+  ctrl += blockIdx.z;
+  if (!should_run<T>(ctrl, check_active)) return;
   count_run(ctrl, tkid);
   constexpr int P = NX + 1;
   constexpr int NEL = NX * NY;
@@ -151,7 +153,9 @@ template <typename T, int N, int C, int MODE, int NT>
 __global__ void __launch_bounds__(NT) k_fx_cols(T *__restrict__ data, int64_t V, int64_t rstride, int ncb,
                                                int64_t ostride, FFTTables tb, const Ctrl *ctrl, int check_active,
                                                int tkid, int twmu) {
-  if (check_active && !ctrl->active) return;
+  data += (int64_t)blockIdx.z * 4 * V * 2;
+  ctrl += blockIdx.z;
+  if (!should_run<T>(ctrl, check_active)) return;
   count_run(ctrl, tkid);
   constexpr int P = C + 1;
   constexpr int NF = MODE == 2 ? 4 : 1;

@@ -3,7 +3,12 @@
 // handover, and the C ABI declared in include/lgf.h.
 #include <cuda_runtime.h>
 
+#include <sys/stat.h>
+#include <unistd.h>
+
 #include <algorithm>
+#include <array>
+#include <map>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -39,8 +44,8 @@ enum KernelId {
   KID_FFT_XY_INV,
   KID_GAUGE,
   KID_UPDATE,
-  KID_UPDATE_ACC,
-  KID_REUNIT,
+  KID_UPDATE_FUSED,
+  KID_UPDATE_FUSED_REUNIT,
   KID_GACC_TO_DOUBLE,
   KID_TRANSFORM_FROM,
   KID_TO_PLANES,
@@ -52,7 +57,7 @@ enum KernelId {
 const char *kKernelBase[KID_COUNT] = {"delta_theta",   "fft_xy_fwd",    "fft_x_fwd",      "fft_y_fwd",
                                       "fft_z_fwd",     "fft_zt_filter", "fft_t_filter",   "fft_z_inv",
                                       "fft_y_inv",     "fft_x_inv",     "fft_xy_inv",     "gauge_g",
-                                      "gauge_update",  "gauge_update_accumulate", "reunitarize",
+                                      "gauge_update",  "gauge_update_fused", "gauge_update_fused_reunit",
                                       "gacc_to_double", "handover_transform", "to_planes", "from_planes",
                                       "set_identity"};
 std::string kKernelNames[2 * KID_COUNT];
@@ -85,6 +90,7 @@ template <typename T> struct State {
 struct lgf_ctx {
   int n[4];
   int64_t V;
+  int nb = 1;  // configurations of this shape held by the context (a batch group); 1 for lgf_create
   Lattice L;
   int device = 0;
   cudaStream_t own_stream = nullptr, stream = nullptr;
@@ -120,6 +126,7 @@ struct lgf_ctx {
   int stage = -1;       // LGF_FP64 or LGF_FP32: precision of the live working links
   int since_reunit = 0;
   bool generic_fft = false;  // force the generic FFT passes (tests compare the two families)
+  int fixed_cols[2] = {0, 0};  // column width of the specialised passes (double, float); 0 = default
   double prev_theta = 0;  // theta and iteration count at the previous chunk boundary
   int prev_iters = 0;
 
@@ -267,12 +274,14 @@ template <typename T, int C, int MODE> const void *cols_kernel(int n) {
     default: return (const void *)k_fx_cols<T, 64, C, MODE, kFixedThreads>;
   }
 }
+template <typename T, int C> const void *cols_kernel_mode(int mode, int n) {
+  if (mode == 0) return cols_kernel<T, C, 0>(n);
+  if (mode == 1) return cols_kernel<T, C, 1>(n);
+  return cols_kernel<T, C, 2>(n);
+}
 template <typename T> const void *fixed_kernel(const Pass &p) {
-  constexpr int C = sizeof(T) == 8 ? 16 : 32;
   if (p.kind == 1) return p.mode == 0 ? plane_kernel<T, false>(p.N) : plane_kernel<T, true>(p.N);
-  if (p.mode == 0) return cols_kernel<T, C, 0>(p.N);
-  if (p.mode == 1) return cols_kernel<T, C, 1>(p.N);
-  return cols_kernel<T, C, 2>(p.N);
+  return p.C == 32 ? cols_kernel_mode<T, 32>(p.mode, p.N) : cols_kernel_mode<T, 16>(p.mode, p.N);
 }
 
 // Specialised plan (5 passes: xy forward, z forward, t forward + filter + inverse, z inverse,
@@ -282,7 +291,8 @@ template <typename T> bool plan_fixed(lgf_ctx *ctx, State<T> &S) {
   for (int mu = 0; mu < 4; ++mu)
     if (!fixed_len(ctx->n[mu])) return false;
   if (Nx != Ny) return false;
-  const int C = sizeof(T) == 8 ? 16 : 32;
+  const int pick = ctx->fixed_cols[sizeof(T) == 8 ? 0 : 1];
+  const int C = pick ? pick : (sizeof(T) == 8 ? 16 : 32);
   const int64_t Nxy = (int64_t)Nx * Ny, Nxyz = Nxy * Nz;
   if (Nxy % C || Nxyz % C) return false;
   const size_t es = sizeof(cx<T>);
@@ -407,9 +417,10 @@ template <typename T> void plan_passes(lgf_ctx *ctx, State<T> &S) {
 
 template <typename T> lgf_status setup_precision(lgf_ctx *ctx, State<T> &S) {
   const int64_t V = ctx->V;
-  TRY(alloc(ctx, &S.U, (size_t)4 * 9 * V * 2));
-  TRY(alloc(ctx, &S.P, (size_t)4 * V * 2));
-  TRY(alloc(ctx, &S.G, (size_t)9 * V * 2));
+  const size_t nb = (size_t)ctx->nb;
+  TRY(alloc(ctx, &S.U, nb * 4 * 9 * V * 2));
+  TRY(alloc(ctx, &S.P, nb * 4 * V * 2));
+  TRY(alloc(ctx, &S.G, nb * 9 * V * 2));
   if (!S.tw[0]) {
     for (int mu = 0; mu < 4; ++mu) {
       const int N = ctx->n[mu];
@@ -447,9 +458,9 @@ template <typename T> lgf_status setup_precision(lgf_ctx *ctx, State<T> &S) {
 lgf_status ensure_common(lgf_ctx *ctx) {
   if (!ctx->partials) {
     ctx->nblocks_site = (int)((ctx->V + NT - 1) / NT);
-    CK(cudaMalloc(&ctx->partials, sizeof(double) * 2 * (size_t)std::max(ctx->nblocks_site, 1)));
-    CK(cudaMalloc(&ctx->ctrl, sizeof(Ctrl)));
-    CK(cudaMemset(ctx->ctrl, 0, sizeof(Ctrl)));
+    CK(cudaMalloc(&ctx->partials, sizeof(double) * 2 * (size_t)std::max(ctx->nblocks_site, 1) * ctx->nb));
+    CK(cudaMalloc(&ctx->ctrl, sizeof(Ctrl) * ctx->nb));
+    CK(cudaMemset(ctx->ctrl, 0, sizeof(Ctrl) * ctx->nb));
   }
   return LGF_OK;
 }
@@ -505,7 +516,7 @@ unsigned grid1(int64_t n, int threads) { return (unsigned)((n + threads - 1) / t
 
 template <typename T> lgf_status launch_delta(lgf_ctx *ctx, State<T> &S, int counts_update, int check_active) {
   TRY(timed_begin(ctx, kid<T>(KID_DELTA)));
-  k_delta<T, NT><<<ctx->nblocks_site, NT, 0, ctx->stream>>>(S.U, S.P, ctx->partials, ctx->ctrl, ctx->L,
+  k_delta<T, NT><<<dim3(ctx->nblocks_site, 1, ctx->nb), NT, 0, ctx->stream>>>(S.U, S.P, ctx->partials, ctx->ctrl, ctx->L,
                                                             counts_update, check_active, kid<T>(KID_DELTA));
   CKL();
   return timed_end(ctx);
@@ -516,18 +527,18 @@ template <typename T> lgf_status launch_filter(lgf_ctx *ctx, State<T> &S, T *dat
     TRY(timed_begin(ctx, kid<T>(p.kid)));
     const int tk = kid<T>(p.kid);
     if (p.kind == 0) {
-      dim3 grid(p.d.nblocks, 4);
+      dim3 grid(p.d.nblocks, 4, ctx->nb);
       k_fft_pass<T><<<grid, p.threads, p.smem, ctx->stream>>>(data, ctx->V, p.d, S.tables, ctx->ctrl, check_active,
                                                                tk);
     } else if (p.kind == 1) {
-      dim3 grid(p.nblocks, 4);
+      dim3 grid(p.nblocks, 4, ctx->nb);
       int64_t V = ctx->V;
       FFTTables tb = S.tables;
       const Ctrl *c = ctx->ctrl;
       void *args[] = {&data, &V, &tb, &c, &check_active, (void *)&tk};
       CK(cudaLaunchKernel(fixed_kernel<T>(p), grid, dim3(p.threads), args, p.smem, ctx->stream));
     } else {
-      dim3 grid(p.nblocks, p.mode == 2 ? 1 : 4);
+      dim3 grid(p.nblocks, p.mode == 2 ? 1 : 4, ctx->nb);
       int64_t V = ctx->V, rs = p.rstride, os = p.ostride;
       int ncb = p.ncb, twmu = p.twmu;
       FFTTables tb = S.tables;
@@ -543,7 +554,7 @@ template <typename T> lgf_status launch_filter(lgf_ctx *ctx, State<T> &S, T *dat
 
 template <typename T> lgf_status launch_gauge(lgf_ctx *ctx, State<T> &S, double alpha, int check_active) {
   TRY(timed_begin(ctx, kid<T>(KID_GAUGE)));
-  k_gauge<T, NT><<<grid1(ctx->V, NT), NT, 0, ctx->stream>>>(S.P, S.G, (T)(0.5 * alpha), ctx->V, ctx->ctrl,
+  k_gauge<T, NT><<<dim3(grid1(ctx->V, NT), 1, ctx->nb), NT, 0, ctx->stream>>>(S.P, S.G, (T)(0.5 * alpha), ctx->V, ctx->ctrl,
                                                             check_active, kid<T>(KID_GAUGE));
   CKL();
   return timed_end(ctx);
@@ -551,26 +562,57 @@ template <typename T> lgf_status launch_gauge(lgf_ctx *ctx, State<T> &S, double 
 
 template <typename T> lgf_status launch_update(lgf_ctx *ctx, State<T> &S, int check_active) {
   TRY(timed_begin(ctx, kid<T>(KID_UPDATE)));
-  k_update<T, NT><<<grid1(ctx->V, NT), NT, 0, ctx->stream>>>(S.U, S.G, ctx->L, ctx->ctrl, check_active,
+  k_update<T, NT><<<dim3(grid1(ctx->V, NT), 1, ctx->nb), NT, 0, ctx->stream>>>(S.U, S.G, ctx->L, ctx->ctrl, check_active,
                                                              kid<T>(KID_UPDATE));
   CKL();
   return timed_end(ctx);
 }
 
 // One iteration of the loop of Algorithm 1 on state S (kernels return at once once the loop stops).
-template <typename T> lgf_status launch_iteration(lgf_ctx *ctx, State<T> &S, double alpha, bool accumulate) {
+template <typename T> lgf_status launch_iteration(lgf_ctx *ctx, State<T> &S, double alpha) {
   TRY(launch_filter<T>(ctx, S, S.P, 1));
   TRY(launch_gauge<T>(ctx, S, alpha, 1));
-  if (accumulate) {
-    TRY(timed_begin(ctx, kid<float>(KID_UPDATE_ACC)));
-    k_update_accumulate<NT><<<grid1(ctx->V, NT), NT, 0, ctx->stream>>>(ctx->s32.U, ctx->s32.G, ctx->Gacc, ctx->L,
-                                                                        ctx->ctrl, kid<float>(KID_UPDATE_ACC));
-    CKL();
-    TRY(timed_end(ctx));
-  } else {
-    TRY(launch_update<T>(ctx, S, 1));
-  }
+  TRY(launch_update<T>(ctx, S, 1));
   return launch_delta<T>(ctx, S, 1, 1);
+}
+
+// Double-stage iteration with the FFT in float (mixed option fft32_final): Delta in double stored
+// packed in float, float FFT passes, g formed in double from the float Delta-tilde, double update.
+lgf_status launch_delta_d2f(lgf_ctx *ctx, int counts_update, int check_active) {
+  TRY(timed_begin(ctx, kid<double>(KID_DELTA)));
+  k_delta<double, NT, float><<<dim3(ctx->nblocks_site, 1, ctx->nb), NT, 0, ctx->stream>>>(
+      ctx->s64.U, ctx->s32.P, ctx->partials, ctx->ctrl, ctx->L, counts_update, check_active, kid<double>(KID_DELTA));
+  CKL();
+  return timed_end(ctx);
+}
+lgf_status launch_iteration_fft32(lgf_ctx *ctx, double alpha) {
+  TRY(launch_filter<float>(ctx, ctx->s32, ctx->s32.P, 2));
+  TRY(timed_begin(ctx, kid<double>(KID_GAUGE)));
+  k_gauge<double, NT, float><<<dim3(grid1(ctx->V, NT), 1, ctx->nb), NT, 0, ctx->stream>>>(
+      ctx->s32.P, ctx->s64.G, 0.5 * alpha, ctx->V, ctx->ctrl, 1, kid<double>(KID_GAUGE));
+  CKL();
+  TRY(timed_end(ctx));
+  TRY(launch_update<double>(ctx, ctx->s64, 1));
+  return launch_delta_d2f(ctx, 1, 1);
+}
+
+// One iteration of the float stage (FP32 / mixed): g is rebuilt inside the update, which also
+// accumulates G and, every reunit_period iterations, reprojects the new links in double precision.
+lgf_status launch_iteration_float(lgf_ctx *ctx, double alpha, bool reunit) {
+  State<float> &S = ctx->s32;
+  TRY(launch_filter<float>(ctx, S, S.P, 1));
+  const int kidx = kid<float>(reunit ? KID_UPDATE_FUSED_REUNIT : KID_UPDATE_FUSED);
+  TRY(timed_begin(ctx, kidx));
+  if (reunit)
+    k_update_fused_f32<NT, true><<<dim3(grid1(ctx->V, NT), 1, ctx->nb), NT, 0, ctx->stream>>>(S.U, S.P, ctx->Gacc, (float)(0.5 * alpha),
+                                                                             ctx->L, ctx->ctrl, kidx);
+  else
+    k_update_fused_f32<NT, false><<<dim3(grid1(ctx->V, NT), 1, ctx->nb), NT, 0, ctx->stream>>>(S.U, S.P, ctx->Gacc,
+                                                                              (float)(0.5 * alpha), ctx->L, ctx->ctrl,
+                                                                              kidx);
+  CKL();
+  TRY(timed_end(ctx));
+  return launch_delta<float>(ctx, S, 1, 1);
 }
 
 lgf_status read_ctrl(lgf_ctx *ctx) {
@@ -585,15 +627,6 @@ lgf_status write_ctrl(lgf_ctx *ctx) {
   CK(cudaMemcpyAsync(ctx->ctrl, &ctx->ctrl_host, sizeof(Ctrl), cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   return LGF_OK;
-}
-
-// Reproject the float links and the accumulated transformation onto SU(3) in double precision.
-lgf_status launch_reunit(lgf_ctx *ctx) {
-  TRY(timed_begin(ctx, kid<float>(KID_REUNIT)));
-  k_reunitarize_fp64<NT><<<grid1(ctx->V * 5, NT), NT, 0, ctx->stream>>>(ctx->s32.U, ctx->Gacc, ctx->V, ctx->ctrl,
-                                                                       kid<float>(KID_REUNIT));
-  CKL();
-  return timed_end(ctx);
 }
 
 // Mixed handover: G from the float accumulation (reprojected in double), then
@@ -655,11 +688,14 @@ lgf_status check_ctx(lgf_ctx *ctx) {
 // msg must be a string with static storage (it is kept by pointer; nothing is allocated). NULL clears it.
 __attribute__((visibility("hidden"))) void lgf_set_static_error(const char *msg) { g_static_literal = msg; }
 
+static lgf_status create_ctx(const int n[4], int nb, lgf_ctx **out);
+
 // ============================================== C ABI ===============================================
 extern "C" {
 
 void lgf_default_options(lgf_options *opt) {
   if (!opt) return;
+  opt->fft32_final = 0;
   opt->precision = LGF_FP64;
   opt->theta_switch = 1e-8;
   opt->reunit_period = 16;
@@ -669,13 +705,22 @@ void lgf_default_options(lgf_options *opt) {
 }
 
 lgf_status lgf_create(int Nx, int Ny, int Nz, int Nt, lgf_ctx **out) {
+  const int n[4] = {Nx, Ny, Nz, Nt};
+  return create_ctx(n, 1, out);
+}
+
+}  // extern "C"
+
+// A context for nb configurations of one lattice shape (nb = 1 for lgf_create).
+static lgf_status create_ctx(const int n[4], int nb, lgf_ctx **out) {
   if (!out) return fail(nullptr, LGF_EINVAL, "null output pointer");
   *out = nullptr;
-  const int n[4] = {Nx, Ny, Nz, Nt};
+  const int Nx = n[0], Ny = n[1], Nz = n[2], Nt = n[3];
   for (int mu = 0; mu < 4; ++mu)
     if (!factor_ok(n[mu]))
       return fail(nullptr, LGF_EINVAL, "lattice extents must be in [2, 1024] and products of 2, 3 and 5");
   lgf_ctx *ctx = new lgf_ctx();
+  ctx->nb = nb;
   for (int mu = 0; mu < 4; ++mu) ctx->n[mu] = n[mu];
   ctx->V = (int64_t)Nx * Ny * Nz * Nt;
   ctx->L.V = ctx->V;
@@ -724,6 +769,8 @@ lgf_status lgf_create(int Nx, int Ny, int Nz, int Nt, lgf_ctx **out) {
   *out = ctx;
   return LGF_OK;
 }
+
+extern "C" {
 
 void lgf_destroy(lgf_ctx *ctx) {
   if (!ctx) return;
@@ -785,6 +832,7 @@ lgf_status lgf_load(lgf_ctx *ctx, const double *links, int precision) {
   ctx->ctrl_host.active = 1;
   ctx->ctrl_host.limit = 0;
   ctx->ctrl_host.threshold = 0;
+  ctx->ctrl_host.stage = precision == LGF_FP64 ? 1 : 0;
   TRY(write_ctrl(ctx));
   if (precision == LGF_FP64) {
     TRY(setup_precision<double>(ctx, ctx->s64));
@@ -793,9 +841,9 @@ lgf_status lgf_load(lgf_ctx *ctx, const double *links, int precision) {
     ctx->stage = LGF_FP64;
   } else {
     TRY(setup_precision<float>(ctx, ctx->s32));
-    TRY(alloc(ctx, &ctx->Gacc, (size_t)9 * V * 2));
+    TRY(alloc(ctx, &ctx->Gacc, (size_t)ctx->nb * 9 * V * 2));
     if (precision == LGF_MIXED) {
-      TRY(alloc(ctx, &ctx->U0, (size_t)4 * 9 * V * 2));
+      TRY(alloc(ctx, &ctx->U0, (size_t)ctx->nb * 4 * 9 * V * 2));
       TRY(to_planes<double>(ctx, src, ctx->U0, 4));
     }
     TRY(to_planes<float>(ctx, src, ctx->s32.U, 4));
@@ -848,8 +896,10 @@ lgf_status lgf_iterate(lgf_ctx *ctx, int max_new, double alpha, double eps, cons
         TRY(handover(ctx));
         ctx->stage = LGF_FP64;
         c.active = 1;
+        c.stage = 1;
         TRY(write_ctrl(ctx));
-        TRY(launch_delta<double>(ctx, ctx->s64, 0, 0));
+        if (o.fft32_final) TRY(launch_delta_d2f(ctx, 0, 0));
+        else TRY(launch_delta<double>(ctx, ctx->s64, 0, 0));
         TRY(read_ctrl(ctx));
         continue;
       }
@@ -872,13 +922,13 @@ lgf_status lgf_iterate(lgf_ctx *ctx, int max_new, double alpha, double eps, cons
     ctx->prev_iters = c.iters;
     for (int k = 0; k < chunk; ++k) {
       if (float_stage) {
-        TRY(launch_iteration<float>(ctx, ctx->s32, alpha, true));
-        if (++ctx->since_reunit >= o.reunit_period) {
-          TRY(launch_reunit(ctx));
-          ctx->since_reunit = 0;
-        }
+        const bool reunit = ++ctx->since_reunit >= o.reunit_period;
+        if (reunit) ctx->since_reunit = 0;
+        TRY(launch_iteration_float(ctx, alpha, reunit));
+      } else if (o.fft32_final && ctx->load_prec == LGF_MIXED) {
+        TRY(launch_iteration_fft32(ctx, alpha));
       } else {
-        TRY(launch_iteration<double>(ctx, ctx->s64, alpha, false));
+        TRY(launch_iteration<double>(ctx, ctx->s64, alpha));
       }
     }
     TRY(read_ctrl(ctx));
@@ -1183,7 +1233,7 @@ lgf_status lgf_kernel_times(lgf_ctx *ctx, const char **name, long *launches, dou
     CK(cudaMemset(ctx->ran_dev, 0, sizeof ran));
     const int loop_kids[] = {KID_DELTA, KID_FFT_XY_FWD, KID_FFT_X_FWD, KID_FFT_Y_FWD, KID_FFT_Z_FWD,
                              KID_FFT_ZT_FILTER, KID_FFT_T_FILTER, KID_FFT_Z_INV, KID_FFT_Y_INV, KID_FFT_X_INV,
-                             KID_FFT_XY_INV, KID_GAUGE, KID_UPDATE, KID_UPDATE_ACC, KID_REUNIT};
+                             KID_FFT_XY_INV, KID_GAUGE, KID_UPDATE, KID_UPDATE_FUSED, KID_UPDATE_FUSED_REUNIT};
     for (int k : loop_kids)
       for (int h = 0; h < 2; ++h) {
         const int i = k + h * KID_COUNT;
@@ -1211,3 +1261,5 @@ lgf_status lgf_kernel_times(lgf_ctx *ctx, const char **name, long *launches, dou
 }
 
 }  // extern "C"
+
+#include "batch.cuh"

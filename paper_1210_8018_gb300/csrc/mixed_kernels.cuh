@@ -1,6 +1,6 @@
 // mixed_kernels.cuh -- kernels of the mixed-precision schedule: float links, FFTs and updates with the
 // accumulated gauge transformation G(x) = g_k(x) ... g_1(x) kept beside them, periodic reprojection of
-// the float links and of G onto SU(3) in double precision, and the handover that rebuilds double
+// the float links onto SU(3) in double precision, and the handover that rebuilds double
 // links as G(x) U0_mu(x) G^+(x + mu) from the saved input U0, so that the double-precision stage
 // starts from links exactly gauge-equivalent to the input.
 #pragma once
@@ -8,24 +8,41 @@
 
 namespace lgf {
 
-// Float update (as k_update) that also accumulates Gacc(x) <- g(x) Gacc(x).
-template <int NT>
-__global__ void __launch_bounds__(NT) k_update_accumulate(float *__restrict__ U, const float *__restrict__ G,
-                                                         float *__restrict__ Gacc, Lattice L, const Ctrl *ctrl,
-                                                         int tkid) {
-  if (!ctrl->active) return;
-  count_run(ctrl, tkid);
+// g(x) = SU(3)-projection of [1 + (alpha/2) Delta-tilde(x)] from the packed float fields.
+__device__ __forceinline__ void gauge_from_packed(const float *P, int64_t V, int64_t s, float half_alpha, m3<float> &g) {
+  unpack_scaled(P, V, s, half_alpha, g);
+  g.e[0].r += 1.0f;
+  g.e[4].r += 1.0f;
+  g.e[8].r += 1.0f;
+  reunitarize(g);
+}
+
+// Float-stage update with g rebuilt in registers: forms g(x) and the four g(x + mu) from the packed
+// Delta-tilde (no g field in memory), accumulates Gacc(x) <- g(x) Gacc(x) and applies
+// U_mu(x) -> g(x) U_mu(x) g^+(x + mu). With REUNIT the new links are projected onto SU(3) in double
+// precision before they are stored (the periodic reunitarisation of the float stage).
+template <int NT, bool REUNIT>
+__global__ void __launch_bounds__(NT) k_update_fused_f32(float *__restrict__ U, const float *__restrict__ P,
+                                                        float *__restrict__ Gacc, float half_alpha, Lattice L,
+                                                        const Ctrl *ctrl, int tkid) {
   const int64_t V = L.V;
+  {
+    const int cfg = blockIdx.z;
+    U += (int64_t)cfg * 36 * V * 2;
+    P += (int64_t)cfg * 4 * V * 2;
+    Gacc += (int64_t)cfg * 9 * V * 2;
+    ctrl += cfg;
+  }
+  if (!stage_active<float>(ctrl)) return;
+  count_run(ctrl, tkid);
   const int64_t s = (int64_t)blockIdx.x * NT + threadIdx.x;
   if (s >= V) return;
   int c[4];
   site_coords(L, s, c);
   m3<float> gx, t, a;
+  gauge_from_packed(P, V, s, half_alpha, gx);
 #pragma unroll
-  for (int e = 0; e < 9; ++e) {
-    gx.e[e] = ldg(G, (int64_t)e * V + s);
-    a.e[e] = ld(Gacc, (int64_t)e * V + s);
-  }
+  for (int e = 0; e < 9; ++e) a.e[e] = ld(Gacc, (int64_t)e * V + s);
   mul(gx, a, t);
 #pragma unroll
   for (int e = 0; e < 9; ++e) st(Gacc, (int64_t)e * V + s, t.e[e]);
@@ -35,37 +52,23 @@ __global__ void __launch_bounds__(NT) k_update_accumulate(float *__restrict__ U,
     float *plane = U + (int64_t)mu * 9 * V * 2;
     m3<float> u, gy;
 #pragma unroll
-    for (int e = 0; e < 9; ++e) {
-      u.e[e] = ld(plane, (int64_t)e * V + s);
-      gy.e[e] = ldg(G, (int64_t)e * V + sf);
-    }
+    for (int e = 0; e < 9; ++e) u.e[e] = ld(plane, (int64_t)e * V + s);
+    gauge_from_packed(P, V, sf, half_alpha, gy);
     mul_rows01(gx, u, t);
     mul_adj_rows01(t, gy, u);
-    complete_row2(u);
+    if constexpr (REUNIT) {
+      m3<double> d;
+#pragma unroll
+      for (int e = 0; e < 6; ++e) d.e[e] = {(double)u.e[e].r, (double)u.e[e].i};
+      reunitarize(d);
+#pragma unroll
+      for (int e = 0; e < 9; ++e) u.e[e] = {(float)d.e[e].r, (float)d.e[e].i};
+    } else {
+      complete_row2(u);
+    }
 #pragma unroll
     for (int e = 0; e < 9; ++e) st(plane, (int64_t)e * V + s, u.e[e]);
   }
-}
-
-// Reproject 5 float matrices per site (4 links and Gacc) onto SU(3) in double precision.
-template <int NT>
-__global__ void __launch_bounds__(NT) k_reunitarize_fp64(float *__restrict__ U, float *__restrict__ Gacc, int64_t V,
-                                                        const Ctrl *ctrl, int tkid) {
-  if (!ctrl->active) return;
-  count_run(ctrl, tkid);
-  const int64_t idx = (int64_t)blockIdx.x * NT + threadIdx.x;
-  if (idx >= 5 * V) return;
-  const int64_t which = idx / V, s = idx - which * V;
-  float *base = which < 4 ? U + which * 9 * V * 2 : Gacc;
-  m3<double> m;
-#pragma unroll
-  for (int e = 0; e < 9; ++e) {
-    const cx<float> v = ld(base, (int64_t)e * V + s);
-    m.e[e] = {(double)v.r, (double)v.i};
-  }
-  reunitarize(m);
-#pragma unroll
-  for (int e = 0; e < 9; ++e) st(base, (int64_t)e * V + s, mkc((float)m.e[e].r, (float)m.e[e].i));
 }
 
 // G64 = SU(3)-projection (in double) of the float accumulation.

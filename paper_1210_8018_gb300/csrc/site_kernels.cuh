@@ -33,11 +33,27 @@ struct Ctrl {
   int hist_len;
   double *hist;          // device history: hist[2k], hist[2k+1] = theta, F after k updates
   unsigned int *ran;     // optional per-kernel counters of launches that did work (timing mode)
+  int stage;             // precision of the live links: 0 float, 1 double; kernels of the other
+                         // precision return at once (a batch launches both in the mixed schedule)
 };
 
 // Count a launch that does work (block 0, thread 0), for the per-kernel timing statistics.
 __device__ __forceinline__ void count_run(const Ctrl *ctrl, int tkid) {
-  if (ctrl->ran && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) atomicAdd(ctrl->ran + tkid, 1u);
+  if (ctrl->ran && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0)
+    atomicAdd(ctrl->ran + tkid, 1u);
+}
+
+// Batched launches: blockIdx.z selects one configuration of a group of equal-shape lattices whose
+// buffers are stored one after the other; this is that configuration's loop control, and the
+// kernel runs only if that configuration's loop is active in this kernel's precision.
+template <typename T> __device__ __forceinline__ bool stage_active(const Ctrl *ctrl) {
+  return ctrl->active && ctrl->stage == (sizeof(T) == 8 ? 1 : 0);
+}
+// check: 0 run unconditionally; 1 run if the loop is active in this kernel's precision; 2 run if the
+// loop is active whatever the stage (a float FFT serving the double stage).
+template <typename T> __device__ __forceinline__ bool should_run(const Ctrl *ctrl, int check) {
+  if (!check) return true;
+  return check == 2 ? ctrl->active != 0 : stage_active<T>(ctrl);
 }
 
 __device__ __forceinline__ int64_t site_back(const Lattice &L, int64_t s, int mu, int c) {
@@ -132,12 +148,20 @@ __device__ __forceinline__ void reduce_and_finalize(double th, double f, double 
 // a1/a2: Delta(x) = sum_nu [U_nu(x-nu) - U_nu(x) - h.c. - trace] (Eqs. 3, 5), theta and F partials.
 // One thread per site; each loads its 4 links and the 4 backward-neighbour links.
 // ---------------------------------------------------------------------------------------------
-template <typename T, int NT>
-__global__ void __launch_bounds__(NT) k_delta(const T *__restrict__ U, T *__restrict__ P, double *partials, Ctrl *ctrl,
+// PT is the type of the packed output (T, or float when a double stage feeds a float FFT).
+template <typename T, int NT, typename PT = T>
+__global__ void __launch_bounds__(NT) k_delta(const T *__restrict__ U, PT *__restrict__ P, double *partials, Ctrl *ctrl,
                                              Lattice L, int counts_update, int check_active, int tkid) {
-  if (check_active && !ctrl->active) return;
-  count_run(ctrl, tkid);
   const int64_t V = L.V;
+  {
+    const int cfg = blockIdx.z;
+    U += (int64_t)cfg * 36 * V * 2;
+    P += (int64_t)cfg * 4 * V * 2;
+    partials += (int64_t)cfg * 2 * gridDim.x;
+    ctrl += cfg;
+  }
+  if (!should_run<T>(ctrl, check_active)) return;
+  count_run(ctrl, tkid);
   const int64_t s = (int64_t)blockIdx.x * NT + threadIdx.x;
   double th = 0.0, f = 0.0;
   if (s < V) {
@@ -168,17 +192,19 @@ __global__ void __launch_bounds__(NT) k_delta(const T *__restrict__ U, T *__rest
     const T a0 = i0 - m, a1 = i1 - m, a2 = i2 - m;
     th = (double)a0 * a0 + (double)a1 * a1 + (double)a2 * a2 +
          2.0 * ((double)norm2(d01) + (double)norm2(d02) + (double)norm2(d12));
-    st(P, s, d01);
-    st(P, V + s, d02);
-    st(P, 2 * V + s, d12);
-    st(P, 3 * V + s, mkc(a0, a1));
+    st(P, s, mkc((PT)d01.r, (PT)d01.i));
+    st(P, V + s, mkc((PT)d02.r, (PT)d02.i));
+    st(P, 2 * V + s, mkc((PT)d12.r, (PT)d12.i));
+    st(P, 3 * V + s, mkc((PT)a0, (PT)a1));
   }
   reduce_and_finalize<NT>(th, f, partials, ctrl, V, counts_update);
 }
 
-// Rebuild the full anti-Hermitian traceless matrix from the packed fields, scaled by a.
-template <typename T> __device__ __forceinline__ void unpack_scaled(const T *P, int64_t V, int64_t s, T a, m3<T> &m) {
-  const cx<T> p0 = ldg(P, s), p1 = ldg(P, V + s), p2 = ldg(P, 2 * V + s), p3 = ldg(P, 3 * V + s);
+// Rebuild the full anti-Hermitian traceless matrix from the packed fields (type PT), scaled by a.
+template <typename T, typename PT = T>
+__device__ __forceinline__ void unpack_scaled(const PT *P, int64_t V, int64_t s, T a, m3<T> &m) {
+  const cx<PT> q0 = ldg(P, s), q1 = ldg(P, V + s), q2 = ldg(P, 2 * V + s), q3 = ldg(P, 3 * V + s);
+  const cx<T> p0 = {(T)q0.r, (T)q0.i}, p1 = {(T)q1.r, (T)q1.i}, p2 = {(T)q2.r, (T)q2.i}, p3 = {(T)q3.r, (T)q3.i};
   m.e[0] = {0, a * p3.r};
   m.e[4] = {0, a * p3.i};
   m.e[8] = {0, -a * (p3.r + p3.i)};
@@ -194,15 +220,21 @@ template <typename T> __device__ __forceinline__ void unpack_scaled(const T *P, 
 // a6: g(x) = SU(3)-projection of [1 + (alpha/2) Delta-tilde(x)] (Eq. 2 expanded to first order in
 // alpha, then reunitarized).
 // ---------------------------------------------------------------------------------------------
-template <typename T, int NT>
-__global__ void __launch_bounds__(NT) k_gauge(const T *__restrict__ P, T *__restrict__ G, T half_alpha, int64_t V,
+template <typename T, int NT, typename PT = T>
+__global__ void __launch_bounds__(NT) k_gauge(const PT *__restrict__ P, T *__restrict__ G, T half_alpha, int64_t V,
                                              const Ctrl *ctrl, int check_active, int tkid) {
-  if (check_active && !ctrl->active) return;
+  {
+    const int cfg = blockIdx.z;
+    P += (int64_t)cfg * 4 * V * 2;
+    G += (int64_t)cfg * 9 * V * 2;
+    ctrl += cfg;
+  }
+  if (!should_run<T>(ctrl, check_active)) return;
   count_run(ctrl, tkid);
   const int64_t s = (int64_t)blockIdx.x * NT + threadIdx.x;
   if (s >= V) return;
   m3<T> g;
-  unpack_scaled(P, V, s, half_alpha, g);
+  unpack_scaled<T, PT>(P, V, s, half_alpha, g);
   g.e[0].r += 1;
   g.e[4].r += 1;
   g.e[8].r += 1;
@@ -217,9 +249,15 @@ __global__ void __launch_bounds__(NT) k_gauge(const T *__restrict__ P, T *__rest
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT) k_update(T *__restrict__ U, const T *__restrict__ G, Lattice L, const Ctrl *ctrl,
                                               int check_active, int tkid) {
-  if (check_active && !ctrl->active) return;
-  count_run(ctrl, tkid);
   const int64_t V = L.V;
+  {
+    const int cfg = blockIdx.z;
+    U += (int64_t)cfg * 36 * V * 2;
+    G += (int64_t)cfg * 9 * V * 2;
+    ctrl += cfg;
+  }
+  if (!should_run<T>(ctrl, check_active)) return;
+  count_run(ctrl, tkid);
   const int64_t s = (int64_t)blockIdx.x * NT + threadIdx.x;
   if (s >= V) return;
   int c[4];

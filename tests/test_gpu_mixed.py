@@ -88,3 +88,19 @@ def test_fp32_precision_fix_reaches_float_floor(lgf):
     with lgf.Lattice(dims) as lat:
         r = lat.fix(U.copy(), 0.08, 1e-9, "fp32", max_iter=500)
     assert r["converged"] and r["theta"] < 1e-9
+
+
+def test_mixed_fft32_final_variant(lgf):
+    """The double stage with a float Fourier filter: same fixed point, theta < 1e-15 in double, exact
+    gauge equivalence, and the iteration count of the all-double final stage within a few."""
+    dims = (16, 16, 16, 16)
+    U = synth.config(dims, 7, 0.6)
+    with lgf.Lattice(dims) as lat:
+        r0 = lat.fix(U.copy(), 0.08, 1e-15, "mixed")
+        Uf = U.copy()
+        r1 = lat.fix(Uf, 0.08, 1e-15, "mixed", fft32_final=True)
+        m = lat.measure(Uf)
+    assert r1["converged"] and r1["theta"] < 1e-15 and m["theta"] < 1e-15
+    assert abs(r1["iters"] - r0["iters"]) <= 3
+    assert abs(r1["F"] - r0["F"]) < 1e-10
+    assert abs(oracle.plaquette(Uf) - oracle.plaquette(U)) < 1e-14
