@@ -78,7 +78,7 @@ def algorithmic(kernel, dims):
         "gauge_update_fused": ((36 + 36 + 18 + 4) * es, 0),
         "gauge_update_fused_reunit": ((36 + 36 + 18 + 4) * es, 4 * 170),
         "gacc_to_double": (9 * 8 + 9 * 16, 170),
-        "handover_transform": (36 * 16 * 2 + 9 * 16, 8 * 216),  # full products (8 x 27 complex MACs)
+        "handover_transform": (36 * 16 * 2 + 9 * 16, 4 * 336),
         "to_planes": (36 * 16 + 36 * es, 0),
         "from_planes": (36 * es + 36 * 16, 0),
         "set_identity": (9 * 8, 0),

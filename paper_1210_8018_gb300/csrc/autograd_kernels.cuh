@@ -116,14 +116,16 @@ __global__ void __launch_bounds__(NT) k_expi(const double *__restrict__ omega, d
   for (int k = 0; k < 3; ++k) lam[(int64_t)k * V + s] = l[k];
 }
 
-// F partials: sum_mu Re Tr[g(x) U_mu(x) g^+(x+mu)] per site, reduced in FP64.
+// F partials: sum_mu Re Tr[g(x) U_mu(x) g^+(x+mu)] per site, reduced in FP64 (kSitesPerThread sites per
+// thread, the grid of k_delta).
 template <int NT>
 __global__ void __launch_bounds__(NT) k_functional_g(const double *__restrict__ U, const double *__restrict__ G,
                                                     double *partials, Ctrl *ctrl, Lattice L) {
   const int64_t V = L.V;
-  const int64_t s = (int64_t)blockIdx.x * NT + threadIdx.x;
   double f = 0.0;
-  if (s < V) {
+  for (int k = 0; k < kSitesPerThread; ++k) {
+    const int64_t s = ((int64_t)blockIdx.x * kSitesPerThread + k) * NT + threadIdx.x;
+    if (s >= V) break;
     int c[4];
     site_coords(L, s, c);
     m3<double> gx;

@@ -457,7 +457,7 @@ template <typename T> lgf_status setup_precision(lgf_ctx *ctx, State<T> &S) {
 
 lgf_status ensure_common(lgf_ctx *ctx) {
   if (!ctx->partials) {
-    ctx->nblocks_site = (int)((ctx->V + NT - 1) / NT);
+    ctx->nblocks_site = (int)((ctx->V + NT * kSitesPerThread - 1) / (NT * kSitesPerThread));
     CK(cudaMalloc(&ctx->partials, sizeof(double) * 2 * (size_t)std::max(ctx->nblocks_site, 1) * ctx->nb));
     CK(cudaMalloc(&ctx->ctrl, sizeof(Ctrl) * ctx->nb));
     CK(cudaMemset(ctx->ctrl, 0, sizeof(Ctrl) * ctx->nb));

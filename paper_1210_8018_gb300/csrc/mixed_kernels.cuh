@@ -110,8 +110,9 @@ __global__ void __launch_bounds__(NT) k_transform_from(const double *__restrict_
       u.e[e] = ldg(Usrc, off + (int64_t)e * V + s);
       gy.e[e] = ldg(G, (int64_t)e * V + sf);
     }
-    mul(gx, u, t);
-    mul_adj(t, gy, u);
+    mul_rows01(gx, u, t);
+    mul_adj_rows01(t, gy, u);
+    complete_row2(u);
 #pragma unroll
     for (int e = 0; e < 9; ++e) st(Udst, off + (int64_t)e * V + s, u.e[e]);
   }

@@ -146,8 +146,30 @@ __device__ __forceinline__ void reduce_and_finalize(double th, double f, double 
 
 // ---------------------------------------------------------------------------------------------
 // a1/a2: Delta(x) = sum_nu [U_nu(x-nu) - U_nu(x) - h.c. - trace] (Eqs. 3, 5), theta and F partials.
-// One thread per site; each loads its 4 links and the 4 backward-neighbour links.
+// Each thread handles kSitesPerThread sites (consecutive threads take consecutive sites). Only the
+// nine real combinations that the anti-Hermitian traceless part needs are accumulated:
+//   (B_01 - conj B_10), (B_02 - conj B_20), (B_12 - conj B_21) and Im B_00, Im B_11, Im B_22,
+// with B = sum_nu [U_nu(x - nu) - U_nu(x)]. The per-site theta and F are formed in the kernel's
+// precision and accumulated in double; the warp, block and global sums are double.
 // ---------------------------------------------------------------------------------------------
+constexpr int kSitesPerThread = 4;
+
+template <typename T>
+__device__ __forceinline__ void accumulate_link(const T *plane, int64_t V, int64_t s, T sign, T acc[9]) {
+  const cx<T> u00 = ldg(plane, s), u01 = ldg(plane, V + s), u02 = ldg(plane, 2 * V + s);
+  const cx<T> u10 = ldg(plane, 3 * V + s), u11 = ldg(plane, 4 * V + s), u12 = ldg(plane, 5 * V + s);
+  const cx<T> u20 = ldg(plane, 6 * V + s), u21 = ldg(plane, 7 * V + s), u22 = ldg(plane, 8 * V + s);
+  acc[0] = fma(sign, u01.r - u10.r, acc[0]);
+  acc[1] = fma(sign, u01.i + u10.i, acc[1]);
+  acc[2] = fma(sign, u02.r - u20.r, acc[2]);
+  acc[3] = fma(sign, u02.i + u20.i, acc[3]);
+  acc[4] = fma(sign, u12.r - u21.r, acc[4]);
+  acc[5] = fma(sign, u12.i + u21.i, acc[5]);
+  acc[6] = fma(sign, u00.i, acc[6]);
+  acc[7] = fma(sign, u11.i, acc[7]);
+  acc[8] = fma(sign, u22.i, acc[8]);
+}
+
 // PT is the type of the packed output (T, or float when a double stage feeds a float FFT).
 template <typename T, int NT, typename PT = T>
 __global__ void __launch_bounds__(NT) k_delta(const T *__restrict__ U, PT *__restrict__ P, double *partials, Ctrl *ctrl,
@@ -162,39 +184,35 @@ __global__ void __launch_bounds__(NT) k_delta(const T *__restrict__ U, PT *__res
   }
   if (!should_run<T>(ctrl, check_active)) return;
   count_run(ctrl, tkid);
-  const int64_t s = (int64_t)blockIdx.x * NT + threadIdx.x;
   double th = 0.0, f = 0.0;
-  if (s < V) {
+#pragma unroll 1
+  for (int k = 0; k < kSitesPerThread; ++k) {
+    const int64_t s = ((int64_t)blockIdx.x * kSitesPerThread + k) * NT + threadIdx.x;
+    if (s >= V) break;
     int c[4];
     site_coords(L, s, c);
-    cx<T> B[9];
+    T acc[9];
 #pragma unroll
-    for (int e = 0; e < 9; ++e) B[e] = {0, 0};
+    for (int e = 0; e < 9; ++e) acc[e] = 0;
+    T fs = 0;
 #pragma unroll
     for (int mu = 0; mu < 4; ++mu) {
-      const int64_t sb = site_back(L, s, mu, c[mu]);
       const T *plane = U + (int64_t)mu * 9 * V * 2;
-#pragma unroll
-      for (int e = 0; e < 9; ++e) {
-        const cx<T> here = ldg(plane, (int64_t)e * V + s);
-        const cx<T> back = ldg(plane, (int64_t)e * V + sb);
-        B[e] = B[e] + (back - here);
-      }
-      // F partial: Re Tr U_mu(x), summed in double
-      f += (double)ldg(plane, s).r + (double)ldg(plane, 4 * V + s).r + (double)ldg(plane, 8 * V + s).r;
+      accumulate_link(plane, V, site_back(L, s, mu, c[mu]), (T)1, acc);  // U_mu(x - mu)
+      accumulate_link(plane, V, s, (T)-1, acc);                          // - U_mu(x)
+      fs += ldg(plane, s).r + ldg(plane, 4 * V + s).r + ldg(plane, 8 * V + s).r;  // Re Tr U_mu(x)
     }
-    // anti-Hermitian part: Delta_ij = B_ij - conj(B_ji); diagonal 2i Im B_ii, then remove trace/3
-    const cx<T> d01 = B[1] - conjg(B[3]);
-    const cx<T> d02 = B[2] - conjg(B[6]);
-    const cx<T> d12 = B[5] - conjg(B[7]);
-    const T i0 = 2 * B[0].i, i1 = 2 * B[4].i, i2 = 2 * B[8].i;
-    const T m = (i0 + i1 + i2) / (T)3;
-    const T a0 = i0 - m, a1 = i1 - m, a2 = i2 - m;
-    th = (double)a0 * a0 + (double)a1 * a1 + (double)a2 * a2 +
-         2.0 * ((double)norm2(d01) + (double)norm2(d02) + (double)norm2(d12));
-    st(P, s, mkc((PT)d01.r, (PT)d01.i));
-    st(P, V + s, mkc((PT)d02.r, (PT)d02.i));
-    st(P, 2 * V + s, mkc((PT)d12.r, (PT)d12.i));
+    // Delta_ij = acc (off-diagonal), Delta_ii = 2i (Im B_ii - mean)
+    const T m = (acc[6] + acc[7] + acc[8]) / (T)3;
+    const T a0 = 2 * (acc[6] - m), a1 = 2 * (acc[7] - m), a2 = 2 * (acc[8] - m);
+    const T ts = a0 * a0 + a1 * a1 + a2 * a2 +
+                 2 * (acc[0] * acc[0] + acc[1] * acc[1] + acc[2] * acc[2] + acc[3] * acc[3] + acc[4] * acc[4] +
+                      acc[5] * acc[5]);
+    th += (double)ts;
+    f += (double)fs;
+    st(P, s, mkc((PT)acc[0], (PT)acc[1]));
+    st(P, V + s, mkc((PT)acc[2], (PT)acc[3]));
+    st(P, 2 * V + s, mkc((PT)acc[4], (PT)acc[5]));
     st(P, 3 * V + s, mkc((PT)a0, (PT)a1));
   }
   reduce_and_finalize<NT>(th, f, partials, ctrl, V, counts_update);
@@ -340,9 +358,10 @@ template <typename T> __global__ void k_unpack_antiherm(const T *__restrict__ P,
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT) k_plaquette(const T *__restrict__ U, double *partials, Lattice L) {
   const int64_t V = L.V;
-  const int64_t s = (int64_t)blockIdx.x * NT + threadIdx.x;
   double acc = 0.0;
-  if (s < V) {
+  for (int k = 0; k < kSitesPerThread; ++k) {
+    const int64_t s = ((int64_t)blockIdx.x * kSitesPerThread + k) * NT + threadIdx.x;
+    if (s >= V) break;
     int c[4];
     site_coords(L, s, c);
     for (int mu = 0; mu < 4; ++mu)
