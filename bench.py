@@ -297,13 +297,14 @@ def run_autograd(args):
         _, tb = _timed(torch, lambda: [lat.functional_grad(U, om, grad) for _ in range(n)])
     out["forward_ms"] = 1e3 * tf / n
     out["backward_ms"] = 1e3 * tb / n
-    Uc = U.clone()
-    res, dt = _timed(torch, lambda: lgf.adam_fix(Uc, target=1e-10, lr=3e-2, max_steps=args.steps * 6000,
-                                                 omega0=om))
-    out["adam"] = {k: v for k, v in res.items() if k != "history"}
-    out["adam"]["time_s"] = dt
-    out["adam"]["theta_trace"] = [(h[0], h[1]) for h in res["history"][::max(1, len(res["history"]) // 20)]]
-    out["value"] = res["theta"]
+    for name, pre, budget in (("adam_fourier_preconditioned", True, args.steps * 600), ("adam", False, args.steps * 6000)):
+        Uc = U.clone()
+        res, dt = _timed(torch, lambda: lgf.adam_fix(Uc, target=1e-10, lr=3e-2, max_steps=budget, omega0=om,
+                                                     precondition=pre))
+        out[name] = {k: v for k, v in res.items() if k != "history"}
+        out[name]["time_s"] = dt
+        out[name]["theta_trace"] = [(h[0], h[1]) for h in res["history"][::max(1, len(res["history"]) // 20)]]
+    out["value"] = out["adam_fourier_preconditioned"]["theta"]
     return out
 
 

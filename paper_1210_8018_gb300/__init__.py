@@ -355,8 +355,36 @@ def LandauF():
     return _LandauF
 
 
+def _gell_mann_basis(device):
+    import torch
+    l = torch.zeros((8, 3, 3), dtype=torch.complex128)
+    l[0, 0, 1] = l[0, 1, 0] = 1
+    l[1, 0, 1], l[1, 1, 0] = -1j, 1j
+    l[2, 0, 0], l[2, 1, 1] = 1, -1
+    l[3, 0, 2] = l[3, 2, 0] = 1
+    l[4, 0, 2], l[4, 2, 0] = -1j, 1j
+    l[5, 1, 2] = l[5, 2, 1] = 1
+    l[6, 1, 2], l[6, 2, 1] = -1j, 1j
+    l[7] = torch.diag(torch.tensor([1, 1, -2], dtype=torch.complex128)) / 3 ** 0.5
+    return l.to(device)
+
+
+def _fourier_precondition(lat, grad, basis, dims):
+    """Apply the p^2_max/p^2 filter of Algorithm 1 to a gradient field (V x 8 coefficients of lambda^a)
+    with the library's FFT kernels: the field is written as the anti-Hermitian traceless matrices
+    i sum_a grad^a lambda^a, filtered element by element, and projected back."""
+    import torch
+    nx, ny, nz, nt = dims
+    M = 1j * torch.einsum("sa,aij->sij", grad.to(torch.complex128), basis)
+    M = M.reshape(nt, nz, ny, nx, 3, 3).contiguous()
+    out = torch.empty_like(M)
+    lat.filter(M, out)
+    # coefficient of i lambda^a: Tr(lambda^a (-i M)) / 2
+    return 0.5 * torch.einsum("aij,sji->sa", basis, -1j * out.reshape(-1, 3, 3)).real.contiguous()
+
+
 def adam_fix(U, target=1e-10, lr=1e-2, max_steps=20000, check_every=20, lr_decay=0.5, min_lr=1e-9,
-             omega0=None):
+             omega0=None, precondition=False):
     """Maximise F_U[exp(i omega)] over omega with torch.optim.Adam (plain gradient information, no
     Fourier acceleration), using the library's forward and backward kernels, until theta of the
     transformed links g U g^+ falls to `target`.
@@ -364,8 +392,9 @@ def adam_fix(U, target=1e-10, lr=1e-2, max_steps=20000, check_every=20, lr_decay
     omega starts at omega0 (default 0) and stays in one coordinate system; every `check_every` steps
     F and theta are evaluated, and the learning rate is multiplied by `lr_decay` whenever F did not
     increase since the previous check (Adam has overshot). At the end g is applied to U in place (an
-    exact FP64 gauge transformation through lgf_update). Returns dict(theta, F, F0, steps, lr,
-    history=[(step, theta, F, lr)])."""
+    exact FP64 gauge transformation through lgf_update). With precondition=True the gradient is first
+    Fourier-accelerated (the p^2_max/p^2 filter of Algorithm 1, applied by the library's FFT kernels).
+    Returns dict(theta, F, F0, steps, lr, history=[(step, theta, F, lr)])."""
     import torch
     dims = dims_of(U)
     V = int(np.prod(dims))
@@ -388,11 +417,15 @@ def adam_fix(U, target=1e-10, lr=1e-2, max_steps=20000, check_every=20, lr_decay
         F, theta = evaluate()
         hist.append((0, theta, F, lr))
         opt = torch.optim.Adam([omega], lr=lr)
+        basis = _gell_mann_basis(U.device) if precondition else None
         step = 0
         while step < max_steps and theta > target and opt.param_groups[0]["lr"] > min_lr:
             opt.zero_grad(set_to_none=False)
             loss = -LF.apply(omega, U, lat)
             loss.backward()
+            if precondition:
+                with torch.no_grad():
+                    omega.grad.copy_(_fourier_precondition(lat, omega.grad, basis, dims))
             opt.step()
             step += 1
             if step % check_every == 0:

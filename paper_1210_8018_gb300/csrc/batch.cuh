@@ -92,15 +92,7 @@ template <typename T> lgf_status apply_fft_choice(lgf_ctx *ctx, State<T> &S, boo
   ctx->generic_fft = generic;
   ctx->fixed_cols[sizeof(T) == 8 ? 0 : 1] = C;
   plan_passes<T>(ctx, S);
-  size_t generic_max = 0;
-  for (auto &p : S.passes) {
-    if (p.kind == 0) generic_max = std::max(generic_max, p.smem);
-    else if (p.smem > 48 * 1024)
-      CK(cudaFuncSetAttribute(fixed_kernel<T>(p), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
-  }
-  if (generic_max > 48 * 1024)
-    CK(cudaFuncSetAttribute(k_fft_pass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)generic_max));
-  return LGF_OK;
+  return opt_in_smem<T>(ctx, S);
 }
 
 // Time the filter passes of the current plan (ms per application, median of 5 after 2 warm-ups).
@@ -214,11 +206,14 @@ template <typename T> T *cfg_mat(T *base, const lgf_ctx *g, int j) { return base
 // Delta, theta and F of configuration j alone (used at load and after a handover).
 template <typename T> lgf_status delta_one(lgf_ctx *g, State<T> &S, int j) {
   lgf_ctx *ctx = g;
-  k_delta<T, NT><<<dim3(g->nblocks_site, 1, 1), NT, 0, g->stream>>>(
-      cfg_links(S.U, g, j), cfg_packed(S.P, g, j), g->partials + (int64_t)j * 2 * g->nblocks_site, g->ctrl + j, g->L,
-      0, 0, 0);
-  CKL();
-  return LGF_OK;
+  return with_fft_type<T>(g, [&](auto tag) -> lgf_status {
+    using FT = decltype(tag);
+    k_delta<T, NT, FT><<<dim3(g->nblocks_site, 1, 1), NT, 0, g->stream>>>(
+        cfg_links(S.U, g, j), reinterpret_cast<FT *>(cfg_packed(S.P, g, j)),
+        g->partials + (int64_t)j * 2 * g->nblocks_site, g->ctrl + j, g->L, 0, 0, 0);
+    CKL();
+    return LGF_OK;
+  });
 }
 
 lgf_status handover_one(lgf_ctx *g, int j) {

@@ -1,0 +1,88 @@
+// df64.cuh -- double-float ("df64") numbers: an unevaluated sum hi + lo of two floats (|lo| <= ulp(hi)/2),
+// a 48-bit significand built from FP32 operations. On this GPU the FP64 pipe runs at 1/64 of the FP32
+// rate, so the Fourier filter of the double-precision path runs in df64: its error (~2^-47 relative to
+// the norm of the field) is far below what the 1e-12 agreement with the FP64 oracle needs, and the
+// filter only sets the direction of the gauge update; links, Delta, g, the update and the theta/F sums
+// stay in IEEE double.
+//
+// Building blocks (error-free transformations): TwoSum (Knuth), FastTwoSum (Dekker, |a| >= |b|) and
+// TwoProd with a fused multiply-add; the double-word operations follow Joldes, Muller, Popescu,
+// "Tight and rigorous error bounds for basic building blocks of double-word arithmetic" (2017):
+// addition here is the "sloppy" variant (its error is bounded relative to |x| + |y|, which is the
+// bound an FFT's normwise error analysis uses), multiplication is DWTimesDW.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace lgf {
+
+struct df64 {
+  float hi, lo;
+};
+
+__host__ __device__ constexpr df64 df64_from_double(double d) {
+  return df64{(float)d, (float)(d - (double)(float)d)};
+}
+__device__ __forceinline__ double df64_to_double(df64 a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ df64 df64_from_double_rt(double d) {
+  const float hi = __double2float_rn(d);
+  return {hi, __double2float_rn(d - (double)hi)};
+}
+
+// (the _rn intrinsics keep the compiler from contracting or reassociating these exact steps)
+__device__ __forceinline__ df64 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ df64 fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ df64 operator+(df64 x, df64 y) {
+  const df64 s = two_sum(x.hi, y.hi);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ df64 operator-(df64 x) { return {-x.hi, -x.lo}; }
+__device__ __forceinline__ df64 operator-(df64 x, df64 y) { return x + (-y); }
+__device__ __forceinline__ df64 operator*(df64 x, df64 y) {
+  const float ch = __fmul_rn(x.hi, y.hi);
+  const float cl1 = __fmaf_rn(x.hi, y.hi, -ch);
+  const float tl1 = __fmaf_rn(x.hi, y.lo, __fmul_rn(x.lo, y.lo));
+  const float cl2 = __fmaf_rn(x.lo, y.hi, tl1);
+  return fast_two_sum(ch, __fadd_rn(cl1, cl2));
+}
+// the double and float fma stay visible beside the df64 overload inside this namespace
+using ::fma;
+__device__ __forceinline__ df64 fma(df64 a, df64 b, df64 c) { return a * b + c; }
+__device__ __forceinline__ bool operator==(df64 a, df64 b) { return a.hi == b.hi && a.lo == b.lo; }
+// x / y: a float quotient refined by one Newton step in df64.
+__device__ __forceinline__ df64 operator/(df64 x, df64 y) {
+  const float q1 = x.hi / y.hi;
+  const df64 r = x - y * df64{q1, 0.f};
+  const float q2 = r.hi / y.hi;
+  return fast_two_sum(q1, q2);
+}
+
+// Constants and conversions for the arithmetic types float, double and df64.
+template <typename T> __host__ __device__ constexpr T kconst(double c) { return (T)c; }
+template <> __host__ __device__ constexpr df64 kconst<df64>(double c) { return df64_from_double(c); }
+
+template <typename D, typename S> struct Conv {
+  __device__ __forceinline__ static D f(S s) { return (D)s; }
+};
+template <> struct Conv<df64, double> {
+  __device__ __forceinline__ static df64 f(double s) { return df64_from_double_rt(s); }
+};
+template <> struct Conv<double, df64> {
+  __device__ __forceinline__ static double f(df64 s) { return df64_to_double(s); }
+};
+template <> struct Conv<df64, df64> {
+  __device__ __forceinline__ static df64 f(df64 s) { return s; }
+};
+template <> struct Conv<df64, float> {
+  __device__ __forceinline__ static df64 f(float s) { return {s, 0.f}; }
+};
+template <typename D, typename S> __device__ __forceinline__ D convert(S s) { return Conv<D, S>::f(s); }
+
+}  // namespace lgf

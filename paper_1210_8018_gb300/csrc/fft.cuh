@@ -63,9 +63,10 @@ template <typename T, bool INV> __device__ __forceinline__ void dft2(cx<T> *v) {
 }
 
 template <typename T, bool INV> __device__ __forceinline__ void dft3(cx<T> *v) {
-  const T h = (T)0.86602540378443864676;  // sqrt(3)/2
+  const T h = kconst<T>(0.86602540378443864676);  // sqrt(3)/2
   const cx<T> s = v[1] + v[2], d = v[1] - v[2];
-  const cx<T> a = {v[0].r - (T)0.5 * s.r, v[0].i - (T)0.5 * s.i};
+  const T half = kconst<T>(0.5);
+  const cx<T> a = {v[0].r - half * s.r, v[0].i - half * s.i};
   const cx<T> b = scale(mul_mi<T, INV>(d), h);  // forward: -i (sqrt3/2) (x1 - x2)
   v[0] = v[0] + s;
   v[1] = a + b;
@@ -81,8 +82,8 @@ template <typename T, bool INV> __device__ __forceinline__ void dft4(cx<T> *v) {
 }
 
 template <typename T, bool INV> __device__ __forceinline__ void dft5(cx<T> *v) {
-  const T c1 = (T)0.30901699437494742410, c2 = (T)-0.80901699437494742410;  // cos(2pi/5), cos(4pi/5)
-  const T s1 = (T)0.95105651629515357212, s2 = (T)0.58778525229247312917;   // sin(2pi/5), sin(4pi/5)
+  const T c1 = kconst<T>(0.30901699437494742410), c2 = kconst<T>(-0.80901699437494742410);  // cos 2pi/5, 4pi/5
+  const T s1 = kconst<T>(0.95105651629515357212), s2 = kconst<T>(0.58778525229247312917);   // sin 2pi/5, 4pi/5
   const cx<T> a1 = v[1] + v[4], b1 = v[1] - v[4], a2 = v[2] + v[3], b2 = v[2] - v[3];
   const cx<T> x0 = v[0];
   v[0] = x0 + a1 + a2;
@@ -101,7 +102,7 @@ template <typename T, bool INV> __device__ __forceinline__ void dft8(cx<T> *v) {
   cx<T> e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
   dft4<T, INV>(e);
   dft4<T, INV>(o);
-  const T h = (T)0.70710678118654752440;  // 1/sqrt(2)
+  const T h = kconst<T>(0.70710678118654752440);  // 1/sqrt(2)
   // twiddles w8^k, k = 0..3 (forward w8 = (1 - i)/sqrt 2)
   const cx<T> o1 = INV ? cx<T>{h * (o[1].r - o[1].i), h * (o[1].r + o[1].i)}
                        : cx<T>{h * (o[1].r + o[1].i), h * (o[1].i - o[1].r)};
@@ -251,7 +252,7 @@ __global__ void __launch_bounds__(512) k_fft_pass(T *__restrict__ data, int64_t 
       const int pt = (int)(s / tb.n[2]);
       const double p2 = __ldg(tb.p2part[0] + px) + __ldg(tb.p2part[1] + py) + __ldg(tb.p2part[2] + pz) +
                         __ldg(tb.p2part[3] + pt);
-      const T w = p2 == 0.0 ? (T)0 : (T)(tb.wscale / p2);
+      const T w = p2 == 0.0 ? kconst<T>(0.0) : convert<T>(tb.wscale / p2);
       tile[e] = scale(tile[e], w);
     }
     __syncthreads();

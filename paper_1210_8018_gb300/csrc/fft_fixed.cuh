@@ -109,8 +109,7 @@ __global__ void __launch_bounds__(NT) k_fx_plane(T *__restrict__ data, int64_t V
   for (int k = 0; k < PER; ++k) {
     const int e = threadIdx.x + k * NT;
     if (e < NEL) {
-      const typename vec2<T>::type v = __ldg(reinterpret_cast<const typename vec2<T>::type *>(src) + e);
-      reg[k] = {v.x, v.y};
+      reg[k] = from_vec<T>(__ldg(reinterpret_cast<const typename vec2<T>::type *>(src) + e));
     }
   }
 #pragma unroll
@@ -131,11 +130,7 @@ __global__ void __launch_bounds__(NT) k_fx_plane(T *__restrict__ data, int64_t V
   for (int k = 0; k < PER; ++k) {
     const int e = threadIdx.x + k * NT;
     if (e < NEL) {
-      const cx<T> v = tile[(e / NX) * P + (e % NX)];
-      typename vec2<T>::type o;
-      o.x = v.r;
-      o.y = v.i;
-      reinterpret_cast<typename vec2<T>::type *>(dst)[e] = o;
+      reinterpret_cast<typename vec2<T>::type *>(dst)[e] = to_vec<T>(tile[(e / NX) * P + (e % NX)]);
     }
   }
 }
@@ -179,9 +174,7 @@ __global__ void __launch_bounds__(NT) k_fx_cols(T *__restrict__ data, int64_t V,
       const int e = threadIdx.x + k * NT;
       if (e < NEL) {
         const int n = e / C, c = e % C;
-        const typename vec2<T>::type v =
-            __ldg(reinterpret_cast<const typename vec2<T>::type *>(src) + base + n * rstride + c);
-        reg[k] = {v.x, v.y};
+        reg[k] = from_vec<T>(__ldg(reinterpret_cast<const typename vec2<T>::type *>(src) + base + n * rstride + c));
       }
     }
 #pragma unroll
@@ -201,20 +194,23 @@ __global__ void __launch_bounds__(NT) k_fx_cols(T *__restrict__ data, int64_t V,
   if constexpr (MODE == 2) {
     // weight of each (row, column): w = p2max / (V (p2_xyz(column) + p2_t(row))), 0 at k = 0
     __shared__ T sxyz[C];
+    __shared__ T srow[N];
     for (int c = threadIdx.x; c < C; c += NT) {
       const int64_t q = col0 + c;
       const int x = (int)(q % tb.n[0]);
       const int64_t r = q / tb.n[0];
       const int y = (int)(r % tb.n[1]);
       const int z = (int)(r / tb.n[1]);
-      sxyz[c] = (T)(__ldg(tb.p2part[0] + x) + __ldg(tb.p2part[1] + y) + __ldg(tb.p2part[2] + z));
+      sxyz[c] = convert<T>(__ldg(tb.p2part[0] + x) + __ldg(tb.p2part[1] + y) + __ldg(tb.p2part[2] + z));
     }
+    for (int n = threadIdx.x; n < N; n += NT) srow[n] = convert<T>(__ldg(tb.p2part[3] + n));
     __syncthreads();
-    const T wscale = (T)tb.wscale;
+    const T wscale = convert<T>(tb.wscale);
+    const T zero = kconst<T>(0.0);
     for (int e = threadIdx.x; e < NEL; e += NT) {
       const int n = e / C, c = e % C;
-      const T p2 = sxyz[c] + (T)__ldg(tb.p2part[3] + n);
-      const T w = p2 == (T)0 ? (T)0 : wscale / p2;
+      const T p2 = sxyz[c] + srow[n];
+      const T w = p2 == zero ? zero : wscale / p2;
 #pragma unroll
       for (int f = 0; f < 4; ++f) {
         cx<T> &v = tile[f * TILE + n * P + c];
@@ -231,11 +227,7 @@ __global__ void __launch_bounds__(NT) k_fx_cols(T *__restrict__ data, int64_t V,
     cx<T> *dst = reinterpret_cast<cx<T> *>(data + (int64_t)field * V * 2);
     for (int e = threadIdx.x; e < NEL; e += NT) {
       const int n = e / C, c = e % C;
-      const cx<T> v = tile[f * TILE + n * P + c];
-      typename vec2<T>::type o;
-      o.x = v.r;
-      o.y = v.i;
-      reinterpret_cast<typename vec2<T>::type *>(dst)[base + n * rstride + c] = o;
+      reinterpret_cast<typename vec2<T>::type *>(dst)[base + n * rstride + c] = to_vec<T>(tile[f * TILE + n * P + c]);
     }
   }
 }

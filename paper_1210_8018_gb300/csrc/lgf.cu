@@ -19,7 +19,7 @@
 
 #include "../../include/lgf.h"
 #include "fft.cuh"
-#include "fft_fixed.cuh"
+#include "fft_dispatch.h"
 #include "autograd_kernels.cuh"
 #include "mixed_kernels.cuh"
 #include "site_kernels.cuh"
@@ -126,6 +126,7 @@ struct lgf_ctx {
   int stage = -1;       // LGF_FP64 or LGF_FP32: precision of the live working links
   int since_reunit = 0;
   bool generic_fft = false;  // force the generic FFT passes (tests compare the two families)
+  bool fft_df64 = true;      // double state: Fourier filter in df64 (LGF_FFT_NATIVE_F64=1: IEEE double)
   int fixed_cols[2] = {0, 0};  // column width of the specialised passes (double, float); 0 = default
   double prev_theta = 0;  // theta and iteration count at the previous chunk boundary
   int prev_iters = 0;
@@ -253,36 +254,8 @@ template <typename T> lgf_status alloc(lgf_ctx *ctx, T **p, size_t count) {
   return LGF_OK;
 }
 
-// Kernel pointers of the specialised passes.
-template <typename T, bool INV> const void *plane_kernel(int n) {
-  switch (n) {
-    case 8: return (const void *)k_fx_plane<T, 8, 8, INV, kFixedThreads>;
-    case 16: return (const void *)k_fx_plane<T, 16, 16, INV, kFixedThreads>;
-    case 24: return (const void *)k_fx_plane<T, 24, 24, INV, kFixedThreads>;
-    case 32: return (const void *)k_fx_plane<T, 32, 32, INV, kFixedThreads>;
-    case 48: return (const void *)k_fx_plane<T, 48, 48, INV, kFixedThreads>;
-    default: return (const void *)k_fx_plane<T, 64, 64, INV, kFixedThreads>;
-  }
-}
-template <typename T, int C, int MODE> const void *cols_kernel(int n) {
-  switch (n) {
-    case 8: return (const void *)k_fx_cols<T, 8, C, MODE, kFixedThreads>;
-    case 16: return (const void *)k_fx_cols<T, 16, C, MODE, kFixedThreads>;
-    case 24: return (const void *)k_fx_cols<T, 24, C, MODE, kFixedThreads>;
-    case 32: return (const void *)k_fx_cols<T, 32, C, MODE, kFixedThreads>;
-    case 48: return (const void *)k_fx_cols<T, 48, C, MODE, kFixedThreads>;
-    default: return (const void *)k_fx_cols<T, 64, C, MODE, kFixedThreads>;
-  }
-}
-template <typename T, int C> const void *cols_kernel_mode(int mode, int n) {
-  if (mode == 0) return cols_kernel<T, C, 0>(n);
-  if (mode == 1) return cols_kernel<T, C, 1>(n);
-  return cols_kernel<T, C, 2>(n);
-}
-template <typename T> const void *fixed_kernel(const Pass &p) {
-  if (p.kind == 1) return p.mode == 0 ? plane_kernel<T, false>(p.N) : plane_kernel<T, true>(p.N);
-  return p.C == 32 ? cols_kernel_mode<T, 32>(p.mode, p.N) : cols_kernel_mode<T, 16>(p.mode, p.N);
-}
+// Kernel pointers of the specialised passes (instantiated in the per-type FFT translation units).
+template <typename T> const void *fixed_kernel(const Pass &p) { return fft_fixed_kernel<T>(p.kind, p.mode, p.N, p.C); }
 
 // Specialised plan (5 passes: xy forward, z forward, t forward + filter + inverse, z inverse,
 // xy inverse) when every extent is one of the fixed lengths and Nx == Ny; false otherwise.
@@ -415,6 +388,53 @@ template <typename T> void plan_passes(lgf_ctx *ctx, State<T> &S) {
   for (auto &p : inv) S.passes.push_back(p);
 }
 
+// Arithmetic type of the Fourier filter of state T: float for the float state; for the double state
+// df64 (two floats) unless the context asks for IEEE double. The packed Delta buffer of the state holds
+// that type (16 bytes per complex number for both double and df64).
+template <typename T, typename Fn> lgf_status with_fft_type(const lgf_ctx *ctx, Fn &&fn) {
+  if constexpr (std::is_same<T, double>::value) {
+    if (ctx->fft_df64) return fn(df64{});
+    return fn(double{});
+  } else {
+    return fn(float{});
+  }
+}
+
+template <typename FT> void fill_twiddles(std::vector<FT> &tw, int N) {
+  for (int j = 0; j < N; ++j) {
+    // w_N^j = exp(-2 pi i j / N) in long double, rounded to FT
+    const long double a = 2.0L * 3.14159265358979323846264338327950288L * (long double)j / (long double)N;
+    tw[2 * j] = (FT)std::cos(a);
+    tw[2 * j + 1] = (FT)(-std::sin(a));
+  }
+}
+template <> void fill_twiddles<df64>(std::vector<df64> &tw, int N) {
+  for (int j = 0; j < N; ++j) {
+    const long double a = 2.0L * 3.14159265358979323846264338327950288L * (long double)j / (long double)N;
+    const long double c = std::cos(a), sn = -std::sin(a);
+    const float ch = (float)c, sh = (float)sn;
+    tw[2 * j] = df64{ch, (float)(c - (long double)ch)};
+    tw[2 * j + 1] = df64{sh, (float)(sn - (long double)sh)};
+  }
+}
+
+// Opt the FFT kernels in to the dynamic shared memory each pass needs (the generic kernel: the
+// largest of its passes).
+template <typename T> lgf_status opt_in_smem(lgf_ctx *ctx, State<T> &S) {
+  return with_fft_type<T>(ctx, [&](auto tag) -> lgf_status {
+    using FT = decltype(tag);
+    size_t generic_max = 0;
+    for (auto &p : S.passes) {
+      if (p.kind == 0) generic_max = std::max(generic_max, p.smem);
+      else if (p.smem > 48 * 1024)
+        CK(cudaFuncSetAttribute(fixed_kernel<FT>(p), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
+    }
+    if (generic_max > 48 * 1024)
+      CK(cudaFuncSetAttribute(fft_generic_kernel<FT>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)generic_max));
+    return LGF_OK;
+  });
+}
+
 template <typename T> lgf_status setup_precision(lgf_ctx *ctx, State<T> &S) {
   const int64_t V = ctx->V;
   const size_t nb = (size_t)ctx->nb;
@@ -424,15 +444,14 @@ template <typename T> lgf_status setup_precision(lgf_ctx *ctx, State<T> &S) {
   if (!S.tw[0]) {
     for (int mu = 0; mu < 4; ++mu) {
       const int N = ctx->n[mu];
-      std::vector<T> tw(2 * N);
-      for (int j = 0; j < N; ++j) {
-        // w_N^j = exp(-2 pi i j / N), evaluated in double with the angle reduced to [0, pi/4] by symmetry
-        const long double a = 2.0L * 3.14159265358979323846264338327950288L * (long double)j / (long double)N;
-        tw[2 * j] = (T)std::cos((double)a);
-        tw[2 * j + 1] = (T)(-std::sin((double)a));
-      }
-      CK(cudaMalloc(&S.tw[mu], sizeof(T) * 2 * N));
-      CK(cudaMemcpy(S.tw[mu], tw.data(), sizeof(T) * 2 * N, cudaMemcpyHostToDevice));
+      TRY(with_fft_type<T>(ctx, [&](auto tag) -> lgf_status {
+        using FT = decltype(tag);
+        std::vector<FT> tw(2 * N);
+        fill_twiddles<FT>(tw, N);
+        CK(cudaMalloc(&S.tw[mu], sizeof(FT) * 2 * N));
+        CK(cudaMemcpy(S.tw[mu], tw.data(), sizeof(FT) * 2 * N, cudaMemcpyHostToDevice));
+        return LGF_OK;
+      }));
     }
     plan_passes<T>(ctx, S);
     for (int mu = 0; mu < 4; ++mu) {
@@ -442,15 +461,7 @@ template <typename T> lgf_status setup_precision(lgf_ctx *ctx, State<T> &S) {
       S.tables.n[mu] = ctx->n[mu];
     }
     S.tables.wscale = ctx->wscale;
-    // opt in to the dynamic shared memory each pass needs (the generic kernel: the largest of its passes)
-    size_t generic_max = 0;
-    for (auto &p : S.passes) {
-      if (p.kind == 0) generic_max = std::max(generic_max, p.smem);
-      else if (p.smem > 48 * 1024)
-        CK(cudaFuncSetAttribute(fixed_kernel<T>(p), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
-    }
-    if (generic_max > 48 * 1024)
-      CK(cudaFuncSetAttribute(k_fft_pass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)generic_max));
+    TRY(opt_in_smem<T>(ctx, S));
   }
   return LGF_OK;
 }
@@ -516,27 +527,39 @@ unsigned grid1(int64_t n, int threads) { return (unsigned)((n + threads - 1) / t
 
 template <typename T> lgf_status launch_delta(lgf_ctx *ctx, State<T> &S, int counts_update, int check_active) {
   TRY(timed_begin(ctx, kid<T>(KID_DELTA)));
-  k_delta<T, NT><<<dim3(ctx->nblocks_site, 1, ctx->nb), NT, 0, ctx->stream>>>(S.U, S.P, ctx->partials, ctx->ctrl, ctx->L,
-                                                            counts_update, check_active, kid<T>(KID_DELTA));
-  CKL();
+  TRY(with_fft_type<T>(ctx, [&](auto tag) -> lgf_status {
+    using FT = decltype(tag);
+    k_delta<T, NT, FT><<<dim3(ctx->nblocks_site, 1, ctx->nb), NT, 0, ctx->stream>>>(
+        S.U, reinterpret_cast<FT *>(S.P), ctx->partials, ctx->ctrl, ctx->L, counts_update, check_active,
+        kid<T>(KID_DELTA));
+    CKL();
+    return LGF_OK;
+  }));
   return timed_end(ctx);
 }
 
-template <typename T> lgf_status launch_filter(lgf_ctx *ctx, State<T> &S, T *data, int check_active) {
+template <typename T> lgf_status launch_filter(lgf_ctx *ctx, State<T> &S, T *data_, int check_active) {
+  return with_fft_type<T>(ctx, [&](auto tag) -> lgf_status {
+  using FT = decltype(tag);
+  FT *data = reinterpret_cast<FT *>(data_);
   for (auto &p : S.passes) {
     TRY(timed_begin(ctx, kid<T>(p.kid)));
     const int tk = kid<T>(p.kid);
     if (p.kind == 0) {
       dim3 grid(p.d.nblocks, 4, ctx->nb);
-      k_fft_pass<T><<<grid, p.threads, p.smem, ctx->stream>>>(data, ctx->V, p.d, S.tables, ctx->ctrl, check_active,
-                                                               tk);
+      int64_t V = ctx->V;
+      PassDesc pd = p.d;
+      FFTTables tb = S.tables;
+      const Ctrl *c = ctx->ctrl;
+      void *args[] = {&data, &V, &pd, &tb, &c, &check_active, (void *)&tk};
+      CK(cudaLaunchKernel(fft_generic_kernel<FT>(), grid, dim3(p.threads), args, p.smem, ctx->stream));
     } else if (p.kind == 1) {
       dim3 grid(p.nblocks, 4, ctx->nb);
       int64_t V = ctx->V;
       FFTTables tb = S.tables;
       const Ctrl *c = ctx->ctrl;
       void *args[] = {&data, &V, &tb, &c, &check_active, (void *)&tk};
-      CK(cudaLaunchKernel(fixed_kernel<T>(p), grid, dim3(p.threads), args, p.smem, ctx->stream));
+      CK(cudaLaunchKernel(fixed_kernel<FT>(p), grid, dim3(p.threads), args, p.smem, ctx->stream));
     } else {
       dim3 grid(p.nblocks, p.mode == 2 ? 1 : 4, ctx->nb);
       int64_t V = ctx->V, rs = p.rstride, os = p.ostride;
@@ -544,19 +567,24 @@ template <typename T> lgf_status launch_filter(lgf_ctx *ctx, State<T> &S, T *dat
       FFTTables tb = S.tables;
       const Ctrl *c = ctx->ctrl;
       void *args[] = {&data, &V, &rs, &ncb, &os, &tb, &c, &check_active, (void *)&tk, &twmu};
-      CK(cudaLaunchKernel(fixed_kernel<T>(p), grid, dim3(p.threads), args, p.smem, ctx->stream));
+      CK(cudaLaunchKernel(fixed_kernel<FT>(p), grid, dim3(p.threads), args, p.smem, ctx->stream));
     }
     CKL();
     TRY(timed_end(ctx));
   }
   return LGF_OK;
+  });
 }
 
 template <typename T> lgf_status launch_gauge(lgf_ctx *ctx, State<T> &S, double alpha, int check_active) {
   TRY(timed_begin(ctx, kid<T>(KID_GAUGE)));
-  k_gauge<T, NT><<<dim3(grid1(ctx->V, NT), 1, ctx->nb), NT, 0, ctx->stream>>>(S.P, S.G, (T)(0.5 * alpha), ctx->V, ctx->ctrl,
-                                                            check_active, kid<T>(KID_GAUGE));
-  CKL();
+  TRY(with_fft_type<T>(ctx, [&](auto tag) -> lgf_status {
+    using FT = decltype(tag);
+    k_gauge<T, NT, FT><<<dim3(grid1(ctx->V, NT), 1, ctx->nb), NT, 0, ctx->stream>>>(
+        reinterpret_cast<const FT *>(S.P), S.G, (T)(0.5 * alpha), ctx->V, ctx->ctrl, check_active, kid<T>(KID_GAUGE));
+    CKL();
+    return LGF_OK;
+  }));
   return timed_end(ctx);
 }
 
@@ -743,6 +771,8 @@ static lgf_status create_ctx(const int n[4], int nb, lgf_ctx **out) {
     // LGF_GENERIC_FFT=1 forces the generic FFT passes (used by the tests to check both families)
     const char *g = std::getenv("LGF_GENERIC_FFT");
     ctx->generic_fft = g && g[0] == '1';
+    const char *nf = std::getenv("LGF_FFT_NATIVE_F64");
+    ctx->fft_df64 = !(nf && nf[0] == '1');
   }
   cudaDeviceGetAttribute(&ctx->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
   // p^2 tables (position -> 4 sin^2(pi k / N)) and the filter scale p^2_max / V
@@ -1016,6 +1046,23 @@ lgf_status lgf_measure(lgf_ctx *ctx, const double *links, double *theta, double 
 }  // extern "C"
 
 // ---------------------------------- single steps ----------------------------------
+// Full site matrices <-> the state's packed buffer (in the state's FFT type).
+template <typename T> static lgf_status pack_field(lgf_ctx *ctx, State<T> &S, const double *src) {
+  return with_fft_type<T>(ctx, [&](auto tag) -> lgf_status {
+    using FT = decltype(tag);
+    k_pack_antiherm<FT><<<grid1(ctx->V, NT), NT, 0, ctx->stream>>>(src, reinterpret_cast<FT *>(S.P), ctx->V);
+    CKL();
+    return LGF_OK;
+  });
+}
+template <typename T> static lgf_status unpack_field(lgf_ctx *ctx, State<T> &S, double *dst) {
+  return with_fft_type<T>(ctx, [&](auto tag) -> lgf_status {
+    using FT = decltype(tag);
+    k_unpack_antiherm<FT><<<grid1(ctx->V, NT), NT, 0, ctx->stream>>>(reinterpret_cast<const FT *>(S.P), dst, ctx->V);
+    CKL();
+    return LGF_OK;
+  });
+}
 template <typename T> static lgf_status step_delta(lgf_ctx *ctx, State<T> &S, const double *src, double *dst,
                                                    double *theta, double *F) {
   const int64_t V = ctx->V;
@@ -1024,8 +1071,7 @@ template <typename T> static lgf_status step_delta(lgf_ctx *ctx, State<T> &S, co
   memset(&ctx->ctrl_host, 0, sizeof(Ctrl));
   TRY(write_ctrl(ctx));
   TRY(launch_delta<T>(ctx, S, 0, 0));
-  k_unpack_antiherm<T><<<grid1(V, NT), NT, 0, ctx->stream>>>(S.P, dst, V);
-  CKL();
+  TRY(unpack_field<T>(ctx, S, dst));
   TRY(read_ctrl(ctx));
   if (theta) *theta = ctx->ctrl_host.theta;
   if (F) *F = ctx->ctrl_host.F;
@@ -1056,11 +1102,10 @@ extern "C" lgf_status lgf_delta(lgf_ctx *ctx, const double *links, double *delta
 
 template <typename T> static lgf_status step_filter(lgf_ctx *ctx, State<T> &S, const double *src, double *dst) {
   const int64_t V = ctx->V;
-  k_pack_antiherm<T><<<grid1(V, NT), NT, 0, ctx->stream>>>(src, S.P, V);
-  CKL();
+  TRY(pack_field<T>(ctx, S, src));
   TRY(launch_filter<T>(ctx, S, S.P, 0));
-  k_unpack_antiherm<T><<<grid1(V, NT), NT, 0, ctx->stream>>>(S.P, dst, V);
-  CKL();
+  TRY(unpack_field<T>(ctx, S, dst));
+  (void)V;
   return LGF_OK;
 }
 
@@ -1089,8 +1134,7 @@ extern "C" lgf_status lgf_filter(lgf_ctx *ctx, const double *delta, double *dtil
 template <typename T> static lgf_status step_gauge(lgf_ctx *ctx, State<T> &S, const double *src, double alpha,
                                                    double *dst) {
   const int64_t V = ctx->V;
-  k_pack_antiherm<T><<<grid1(V, NT), NT, 0, ctx->stream>>>(src, S.P, V);
-  CKL();
+  TRY(pack_field<T>(ctx, S, src));
   TRY(launch_gauge<T>(ctx, S, alpha, 0));
   k_planes_to_aos<T><<<grid1(V, NT), NT, 0, ctx->stream>>>(S.G, dst, V, 1);
   CKL();

@@ -10,6 +10,8 @@
 //   Delta is anti-Hermitian and traceless, so these 8 reals determine it; the Fourier filter is real
 //   and even in k, so it maps each packed field onto the packed field of the filtered matrix.
 #pragma once
+#include <type_traits>
+
 #include "su3.cuh"
 
 namespace lgf {
@@ -210,10 +212,10 @@ __global__ void __launch_bounds__(NT) k_delta(const T *__restrict__ U, PT *__res
                       acc[5] * acc[5]);
     th += (double)ts;
     f += (double)fs;
-    st(P, s, mkc((PT)acc[0], (PT)acc[1]));
-    st(P, V + s, mkc((PT)acc[2], (PT)acc[3]));
-    st(P, 2 * V + s, mkc((PT)acc[4], (PT)acc[5]));
-    st(P, 3 * V + s, mkc((PT)a0, (PT)a1));
+    st(P, s, mkc(convert<PT>(acc[0]), convert<PT>(acc[1])));
+    st(P, V + s, mkc(convert<PT>(acc[2]), convert<PT>(acc[3])));
+    st(P, 2 * V + s, mkc(convert<PT>(acc[4]), convert<PT>(acc[5])));
+    st(P, 3 * V + s, mkc(convert<PT>(a0), convert<PT>(a1)));
   }
   reduce_and_finalize<NT>(th, f, partials, ctrl, V, counts_update);
 }
@@ -222,7 +224,8 @@ __global__ void __launch_bounds__(NT) k_delta(const T *__restrict__ U, PT *__res
 template <typename T, typename PT = T>
 __device__ __forceinline__ void unpack_scaled(const PT *P, int64_t V, int64_t s, T a, m3<T> &m) {
   const cx<PT> q0 = ldg(P, s), q1 = ldg(P, V + s), q2 = ldg(P, 2 * V + s), q3 = ldg(P, 3 * V + s);
-  const cx<T> p0 = {(T)q0.r, (T)q0.i}, p1 = {(T)q1.r, (T)q1.i}, p2 = {(T)q2.r, (T)q2.i}, p3 = {(T)q3.r, (T)q3.i};
+  const cx<T> p0 = {convert<T>(q0.r), convert<T>(q0.i)}, p1 = {convert<T>(q1.r), convert<T>(q1.i)};
+  const cx<T> p2 = {convert<T>(q2.r), convert<T>(q2.i)}, p3 = {convert<T>(q3.r), convert<T>(q3.i)};
   m.e[0] = {0, a * p3.r};
   m.e[4] = {0, a * p3.i};
   m.e[8] = {0, -a * (p3.r + p3.i)};
@@ -333,22 +336,23 @@ __global__ void k_planes_to_aos(const T *__restrict__ Pl, double *__restrict__ A
   }
 }
 
-// Full site matrices (AoS double) <-> packed anti-Hermitian traceless fields (planes, T).
-template <typename T> __global__ void k_pack_antiherm(const double *__restrict__ A, T *__restrict__ P, int64_t V) {
+// Full site matrices (AoS double) <-> packed anti-Hermitian traceless fields (planes of PT).
+template <typename PT> __global__ void k_pack_antiherm(const double *__restrict__ A, PT *__restrict__ P, int64_t V) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= V) return;
   const double2 *m = reinterpret_cast<const double2 *>(A) + s * 9;
-  st(P, s, mkc((T)m[1].x, (T)m[1].y));
-  st(P, V + s, mkc((T)m[2].x, (T)m[2].y));
-  st(P, 2 * V + s, mkc((T)m[5].x, (T)m[5].y));
-  st(P, 3 * V + s, mkc((T)m[0].y, (T)m[4].y));
+  st(P, s, mkc(convert<PT>(m[1].x), convert<PT>(m[1].y)));
+  st(P, V + s, mkc(convert<PT>(m[2].x), convert<PT>(m[2].y)));
+  st(P, 2 * V + s, mkc(convert<PT>(m[5].x), convert<PT>(m[5].y)));
+  st(P, 3 * V + s, mkc(convert<PT>(m[0].y), convert<PT>(m[4].y)));
 }
 
-template <typename T> __global__ void k_unpack_antiherm(const T *__restrict__ P, double *__restrict__ A, int64_t V) {
+template <typename PT> __global__ void k_unpack_antiherm(const PT *__restrict__ P, double *__restrict__ A, int64_t V) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= V) return;
+  using T = typename std::conditional<sizeof(PT) == 4, float, double>::type;
   m3<T> m;
-  unpack_scaled(P, V, s, (T)1, m);
+  unpack_scaled<T, PT>(P, V, s, (T)1, m);
   double2 *dst = reinterpret_cast<double2 *>(A) + s * 9;
 #pragma unroll
   for (int e = 0; e < 9; ++e) dst[e] = make_double2((double)m.e[e].r, (double)m.e[e].i);

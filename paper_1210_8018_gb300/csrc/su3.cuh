@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "df64.cuh"
+
 namespace lgf {
 
 template <typename T> struct cx {
@@ -12,6 +14,7 @@ template <typename T> struct cx {
 template <typename T> struct vec2;
 template <> struct vec2<double> { using type = double2; };
 template <> struct vec2<float> { using type = float2; };
+template <> struct vec2<df64> { using type = float4; };  // (re.hi, re.lo, im.hi, im.lo)
 
 template <typename T> __device__ __forceinline__ cx<T> mkc(T r, T i) { return cx<T>{r, i}; }
 template <typename T> __device__ __forceinline__ cx<T> operator+(cx<T> a, cx<T> b) { return {a.r + b.r, a.i + b.i}; }
@@ -44,20 +47,26 @@ template <typename T> __device__ __forceinline__ cx<T> cross_cj(cx<T> a, cx<T> b
   return {p.r - q.r, -(p.i - q.i)};
 }
 
-// Read-only global load / store of one complex element.
-template <typename T> __device__ __forceinline__ cx<T> ldg(const T *base, int64_t idx) {
-  typename vec2<T>::type v = __ldg(reinterpret_cast<const typename vec2<T>::type *>(base) + idx);
-  return {v.x, v.y};
-}
-template <typename T> __device__ __forceinline__ cx<T> ld(const T *base, int64_t idx) {
-  typename vec2<T>::type v = reinterpret_cast<const typename vec2<T>::type *>(base)[idx];
-  return {v.x, v.y};
-}
-template <typename T> __device__ __forceinline__ void st(T *base, int64_t idx, cx<T> a) {
+// Vector register form of one complex number, and back.
+template <typename T> __device__ __forceinline__ cx<T> from_vec(typename vec2<T>::type v) { return {v.x, v.y}; }
+template <> __device__ __forceinline__ cx<df64> from_vec<df64>(float4 v) { return {{v.x, v.y}, {v.z, v.w}}; }
+template <typename T> __device__ __forceinline__ typename vec2<T>::type to_vec(cx<T> a) {
   typename vec2<T>::type v;
   v.x = a.r;
   v.y = a.i;
-  reinterpret_cast<typename vec2<T>::type *>(base)[idx] = v;
+  return v;
+}
+template <> __device__ __forceinline__ float4 to_vec<df64>(cx<df64> a) { return make_float4(a.r.hi, a.r.lo, a.i.hi, a.i.lo); }
+
+// Read-only global load / store of one complex element (base counts real components of type T).
+template <typename T> __device__ __forceinline__ cx<T> ldg(const T *base, int64_t idx) {
+  return from_vec<T>(__ldg(reinterpret_cast<const typename vec2<T>::type *>(base) + idx));
+}
+template <typename T> __device__ __forceinline__ cx<T> ld(const T *base, int64_t idx) {
+  return from_vec<T>(reinterpret_cast<const typename vec2<T>::type *>(base)[idx]);
+}
+template <typename T> __device__ __forceinline__ void st(T *base, int64_t idx, cx<T> a) {
+  reinterpret_cast<typename vec2<T>::type *>(base)[idx] = to_vec<T>(a);
 }
 
 template <typename T> struct m3 {
