@@ -57,9 +57,10 @@ def algorithmic(kernel, dims):
     es = 16 if prec == "f64" else 8
     nx, ny, nz, nt = dims
     lg = {k: np.log2(n) for k, n in zip("xyzt", dims)}
+    lp = 9 if prec == "f64" else 6  # planes per link: float links keep rows 0-1 (row 2 rebuilt on load)
     table = {
         # 4 links read (the backward neighbours are the same data), 4 packed Delta written
-        "delta_theta": ((36 + 4) * es, 190),
+        "delta_theta": ((4 * lp + 4) * es, 190),
         # read + write 4 packed fields; FFT flops 5 N log2 N per field per axis per direction
         "fft_xy_fwd": (8 * es, 4 * 5 * (lg["x"] + lg["y"])),
         "fft_xy_inv": (8 * es, 4 * 5 * (lg["x"] + lg["y"])),
@@ -72,16 +73,16 @@ def algorithmic(kernel, dims):
         "gauge_g": ((4 + 9) * es, 160),
         # links read and written, g read (neighbours are the same data); per link rows 0-1 of
         # g U (18 complex MACs) and of (g U) g^+ (18), row 2 by a cross product: 168 FMA = 336 flop
-        "gauge_update": ((36 + 36 + 9) * es, 4 * 336),
-        # float stage: links read and written, G read and written, packed Delta-tilde read (g is
+        "gauge_update": ((4 * lp * 2 + 9) * es, 4 * 336),
+        # float stage: links read and written, G read and written (rows 0-1), packed Delta-tilde read (g is
         # rebuilt in registers); the _reunit variant also projects the new links in double precision
-        "gauge_update_fused": ((36 + 36 + 18 + 4) * es, 0),
-        "gauge_update_fused_reunit": ((36 + 36 + 18 + 4) * es, 4 * 170),
-        "gacc_to_double": (9 * 8 + 9 * 16, 170),
+        "gauge_update_fused": ((4 * lp * 2 + 12 + 4) * es, 0),
+        "gauge_update_fused_reunit": ((4 * lp * 2 + 12 + 4) * es, 4 * 170),
+        "gacc_to_double": (6 * 8 + 9 * 16, 170),
         "handover_transform": (36 * 16 * 2 + 9 * 16, 4 * 336),
-        "to_planes": (36 * 16 + 36 * es, 0),
-        "from_planes": (36 * es + 36 * 16, 0),
-        "set_identity": (9 * 8, 0),
+        "to_planes": (36 * 16 + 4 * lp * es, 0),
+        "from_planes": (4 * lp * es + 36 * 16, 0),
+        "set_identity": (6 * 8, 0),
     }
     b, f = table[name]
     return b * V, f * V, prec
@@ -297,14 +298,17 @@ def run_autograd(args):
         _, tb = _timed(torch, lambda: [lat.functional_grad(U, om, grad) for _ in range(n)])
     out["forward_ms"] = 1e3 * tf / n
     out["backward_ms"] = 1e3 * tb / n
-    for name, pre, budget in (("adam_fourier_preconditioned", True, args.steps * 600), ("adam", False, args.steps * 6000)):
+    runs = (("adam", dict(optimizer="adam", lr=3e-2, max_steps=args.steps * 6000)),
+            ("sgd_fourier_preconditioned",
+             dict(optimizer="sgd", precondition=True, lr=24 * 0.08 * V, rebase_every=1, check_every=1,
+                  max_steps=args.steps * 100)))
+    for name, kw in runs:
         Uc = U.clone()
-        res, dt = _timed(torch, lambda: lgf.adam_fix(Uc, target=1e-10, lr=3e-2, max_steps=budget, omega0=om,
-                                                     precondition=pre))
+        res, dt = _timed(torch, lambda: lgf.adam_fix(Uc, target=1e-10, omega0=om, **kw))
         out[name] = {k: v for k, v in res.items() if k != "history"}
         out[name]["time_s"] = dt
         out[name]["theta_trace"] = [(h[0], h[1]) for h in res["history"][::max(1, len(res["history"]) // 20)]]
-    out["value"] = out["adam_fourier_preconditioned"]["theta"]
+    out["value"] = out["adam"]["theta"]
     return out
 
 

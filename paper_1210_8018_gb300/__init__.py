@@ -384,22 +384,31 @@ def _fourier_precondition(lat, grad, basis, dims):
 
 
 def adam_fix(U, target=1e-10, lr=1e-2, max_steps=20000, check_every=20, lr_decay=0.5, min_lr=1e-9,
-             omega0=None, precondition=False):
-    """Maximise F_U[exp(i omega)] over omega with torch.optim.Adam (plain gradient information, no
-    Fourier acceleration), using the library's forward and backward kernels, until theta of the
-    transformed links g U g^+ falls to `target`.
+             omega0=None, precondition=False, optimizer="adam", rebase_every=0):
+    """Maximise F_U[exp(i omega)] over omega with a torch optimiser, using the library's forward and
+    backward kernels, until theta of the transformed links g U g^+ falls to `target`.
 
-    omega starts at omega0 (default 0) and stays in one coordinate system; every `check_every` steps
-    F and theta are evaluated, and the learning rate is multiplied by `lr_decay` whenever F did not
-    increase since the previous check (Adam has overshot). At the end g is applied to U in place (an
-    exact FP64 gauge transformation through lgf_update). With precondition=True the gradient is first
-    Fourier-accelerated (the p^2_max/p^2 filter of Algorithm 1, applied by the library's FFT kernels).
-    Returns dict(theta, F, F0, steps, lr, history=[(step, theta, F, lr)])."""
+    optimizer="adam": torch.optim.Adam on the plain gradient (no Fourier acceleration). omega starts at
+    omega0 (default 0); every `check_every` steps F and theta are evaluated, and the learning rate is
+    multiplied by `lr_decay` whenever F did not increase since the previous check.
+    optimizer="sgd": torch.optim.SGD. With precondition=True the gradient first passes through the
+    p^2_max/p^2 filter of Algorithm 1 (the library's FFT kernels); lr = 24 alpha V with re-basing after
+    every step (rebase_every=1: g is absorbed into U and omega reset to 0) reproduces the step of
+    Algorithm 1 with the exponential in place of its first-order expansion.
+    Re-basing applies g to U exactly (FP64, lgf_update) and starts a new optimiser (moments refer to the
+    old coordinates). At the end g is applied to U in place. Returns dict(theta, F, F0, steps, lr,
+    history=[(step, theta, F, lr)])."""
     import torch
     dims = dims_of(U)
     V = int(np.prod(dims))
     LF = LandauF()
     hist = []
+
+    def make_opt(rate):
+        if optimizer == "sgd":
+            return torch.optim.SGD([omega], lr=rate)
+        return torch.optim.Adam([omega], lr=rate)
+
     with Lattice(dims) as lat:
         omega = torch.zeros((V, 8), dtype=torch.float64, device=U.device) if omega0 is None else omega0.clone()
         omega = omega.contiguous().requires_grad_(True)
@@ -416,7 +425,7 @@ def adam_fix(U, target=1e-10, lr=1e-2, max_steps=20000, check_every=20, lr_decay
         F0 = lat.measure(U)["F"]
         F, theta = evaluate()
         hist.append((0, theta, F, lr))
-        opt = torch.optim.Adam([omega], lr=lr)
+        opt = make_opt(lr)
         basis = _gell_mann_basis(U.device) if precondition else None
         step = 0
         while step < max_steps and theta > target and opt.param_groups[0]["lr"] > min_lr:
@@ -428,13 +437,19 @@ def adam_fix(U, target=1e-10, lr=1e-2, max_steps=20000, check_every=20, lr_decay
                     omega.grad.copy_(_fourier_precondition(lat, omega.grad, basis, dims))
             opt.step()
             step += 1
-            if step % check_every == 0:
+            rebase = rebase_every > 0 and step % rebase_every == 0
+            if step % check_every == 0 or rebase:
                 F_prev = F
                 F, theta = evaluate()
-                if F <= F_prev:
+                if F <= F_prev and optimizer == "adam":
                     for pg in opt.param_groups:
                         pg["lr"] *= lr_decay
                 hist.append((step, theta, F, opt.param_groups[0]["lr"]))
+                if rebase:
+                    U.copy_(Ut)
+                    with torch.no_grad():
+                        omega.zero_()
+                    opt = make_opt(opt.param_groups[0]["lr"])
         F, theta = evaluate()
         U.copy_(Ut)
     return dict(theta=theta, F=F, F0=F0, steps=step, lr=opt.param_groups[0]["lr"], history=hist)

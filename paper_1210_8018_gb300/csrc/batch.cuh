@@ -199,9 +199,12 @@ lgf_status bfail(lgf_batch *b, lgf_status st, const std::string &msg) {
   } while (0)
 
 // Plane-offset helpers for configuration j of a group.
-template <typename T> T *cfg_links(T *base, const lgf_ctx *g, int j) { return base + (int64_t)j * 36 * g->V * 2; }
+template <typename T> T *cfg_links(T *base, const lgf_ctx *g, int j) {
+  return base + (int64_t)j * 4 * LinkStore<T>::planes * g->V * 2;
+}
 template <typename T> T *cfg_packed(T *base, const lgf_ctx *g, int j) { return base + (int64_t)j * 4 * g->V * 2; }
 template <typename T> T *cfg_mat(T *base, const lgf_ctx *g, int j) { return base + (int64_t)j * 9 * g->V * 2; }
+float *cfg_gacc(float *base, const lgf_ctx *g, int j) { return base + (int64_t)j * 6 * g->V * 2; }  // rows 0-1
 
 // Delta, theta and F of configuration j alone (used at load and after a handover).
 template <typename T> lgf_status delta_one(lgf_ctx *g, State<T> &S, int j) {
@@ -218,7 +221,7 @@ template <typename T> lgf_status delta_one(lgf_ctx *g, State<T> &S, int j) {
 
 lgf_status handover_one(lgf_ctx *g, int j) {
   lgf_ctx *ctx = g;
-  k_gacc_to_double<NT><<<grid1(g->V, NT), NT, 0, g->stream>>>(cfg_mat(g->Gacc, g, j), cfg_mat(g->s64.G, g, j), g->V);
+  k_gacc_to_double<NT><<<grid1(g->V, NT), NT, 0, g->stream>>>(cfg_gacc(g->Gacc, g, j), cfg_mat(g->s64.G, g, j), g->V);
   CKL();
   k_transform_from<NT><<<grid1(g->V, NT), NT, 0, g->stream>>>(cfg_links(g->U0, g, j), cfg_links(g->s64.U, g, j),
                                                               cfg_mat(g->s64.G, g, j), g->L);
@@ -310,7 +313,7 @@ lgf_status lgf_batch_fix(lgf_batch *b, double *const *links, double alpha, doubl
     }
     if (has_float) {
       BTRY(g, setup_precision<float>(g, g->s32));
-      BTRY(g, alloc(g, &g->Gacc, (size_t)g->nb * 9 * g->V * 2));
+      BTRY(g, alloc(g, &g->Gacc, (size_t)g->nb * 6 * g->V * 2));
       if (prec == LGF_MIXED) BTRY(g, alloc(g, &g->U0, (size_t)g->nb * 4 * 9 * g->V * 2));
       TuneEntry e;
       if (b->autotune) BTRY(g, autotune_fft<float>(g, g->s32, &e));
@@ -328,7 +331,7 @@ lgf_status lgf_batch_fix(lgf_batch *b, double *const *links, double alpha, doubl
     } else {
       if (prec == LGF_MIXED) BTRY(g, to_planes<double>(g, src, cfg_links(g->U0, g, j), 4));
       BTRY(g, to_planes<float>(g, src, cfg_links(g->s32.U, g, j), 4));
-      k_set_identity<<<grid1(g->V, NT), NT, 0, g->stream>>>(cfg_mat(g->Gacc, g, j), g->V);
+      k_set_identity<<<grid1(g->V, NT), NT, 0, g->stream>>>(cfg_gacc(g->Gacc, g, j), g->V);
       CKL();
     }
   }

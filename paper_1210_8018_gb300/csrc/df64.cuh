@@ -71,11 +71,45 @@ template <> __host__ __device__ constexpr df64 kconst<df64>(double c) { return d
 template <typename D, typename S> struct Conv {
   __device__ __forceinline__ static D f(S s) { return (D)s; }
 };
+// double -> df64 with integer operations only (the FP64 pipe is the scarce resource): hi takes the
+// sign, the exponent and the top 23 stored mantissa bits (exact), lo the remaining 29 bits rounded to
+// float and scaled; then the pair is renormalised. Magnitudes below 2^-126 (and zero) give 0, and a
+// remainder below 2^-126 is dropped: both are far below the roundoff of the fields converted here.
+__device__ __forceinline__ df64 df64_split_bits(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned hi32 = (unsigned)(b >> 32), lo32 = (unsigned)b;
+  const int ed = (int)((hi32 >> 20) & 0x7FF);
+  const int ef = ed - 1023 + 127;
+  const unsigned sign = hi32 & 0x80000000u;
+  if (ef < 1) return {0.f, 0.f};
+  if (ef > 254) {  // beyond float range: infinity, or NaN kept as NaN (integer operations only)
+    const bool nan = ed == 0x7FF && (((hi32 & 0xFFFFFu) | lo32) != 0);
+    return {__uint_as_float(sign | 0x7F800000u | (nan ? 0x400000u : 0u)), 0.f};
+  }
+  const float hi = __uint_as_float(sign | ((unsigned)ef << 23) | ((hi32 & 0xFFFFFu) << 3) | (lo32 >> 29));
+  const int es = ed - 1075 + 127;  // exponent of 2^(e - 52) as a float
+  float lo = 0.f;  // the truncated remainder has the sign of d
+  if (es >= 1) {
+    const float mag = (float)(lo32 & 0x1FFFFFFFu) * __uint_as_float((unsigned)es << 23);
+    lo = sign ? -mag : mag;
+  }
+  return fast_two_sum(hi, lo);
+}
+// df64 -> double: each float is widened with integer operations (exact); one FP64 addition remains.
+__device__ __forceinline__ double widen_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ef = (u >> 23) & 0xFFu;
+  if (ef == 0) return 0.0;  // zero (and float subnormals, far below the roundoff here)
+  const unsigned long long bits = ((unsigned long long)(u & 0x80000000u) << 32) |
+                                  ((unsigned long long)(ef == 0xFFu ? 0x7FFu : ef + 896u) << 52) |
+                                  ((unsigned long long)(u & 0x7FFFFFu) << 29);  // Inf/NaN map to Inf/NaN
+  return __longlong_as_double((long long)bits);
+}
 template <> struct Conv<df64, double> {
-  __device__ __forceinline__ static df64 f(double s) { return df64_from_double_rt(s); }
+  __device__ __forceinline__ static df64 f(double s) { return df64_split_bits(s); }
 };
 template <> struct Conv<double, df64> {
-  __device__ __forceinline__ static double f(df64 s) { return df64_to_double(s); }
+  __device__ __forceinline__ static double f(df64 s) { return widen_bits(s.hi) + widen_bits(s.lo); }
 };
 template <> struct Conv<df64, df64> {
   __device__ __forceinline__ static df64 f(df64 s) { return s; }

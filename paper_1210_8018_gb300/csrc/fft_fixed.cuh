@@ -141,10 +141,12 @@ __global__ void __launch_bounds__(NT) k_fx_plane(T *__restrict__ data, int64_t V
 // (b % ncb) * C .. + C of outer slice b / ncb (outer stride `ostride`).
 //   MODE 0: forward (one field per block, blockIdx.y = field)
 //   MODE 1: inverse (one field per block)
-//   MODE 2: forward + filter + inverse, all four fields per block; this pass must be the last axis
-//           (t), so that the columns enumerate x, y, z.
+//   MODE 2: forward + filter + inverse, FPB fields per block (blockIdx.y selects the group of FPB
+//           fields): with FPB = 4 the weight of a site is computed once for all four fields (worth it
+//           when a weight is expensive, as in df64); in float FPB = 1 keeps the tiles small. This pass
+//           must be the last axis (t), so that the columns enumerate x, y, z.
 // ---------------------------------------------------------------------------------------------
-template <typename T, int N, int C, int MODE, int NT>
+template <typename T, int N, int C, int MODE, int NT, int FPB = 4>
 __global__ void __launch_bounds__(NT) k_fx_cols(T *__restrict__ data, int64_t V, int64_t rstride, int ncb,
                                                int64_t ostride, FFTTables tb, const Ctrl *ctrl, int check_active,
                                                int tkid, int twmu) {
@@ -153,7 +155,7 @@ __global__ void __launch_bounds__(NT) k_fx_cols(T *__restrict__ data, int64_t V,
   if (!should_run<T>(ctrl, check_active)) return;
   count_run(ctrl, tkid);
   constexpr int P = C + 1;
-  constexpr int NF = MODE == 2 ? 4 : 1;
+  constexpr int NF = MODE == 2 ? FPB : 1;
   constexpr int TILE = N * P;
   constexpr int NEL = N * C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -166,7 +168,7 @@ __global__ void __launch_bounds__(NT) k_fx_cols(T *__restrict__ data, int64_t V,
   constexpr int PER = (NEL + NT - 1) / NT;
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
-    const int field = MODE == 2 ? f : (int)blockIdx.y;
+    const int field = MODE == 2 ? (int)blockIdx.y * FPB + f : (int)blockIdx.y;
     const cx<T> *src = reinterpret_cast<const cx<T> *>(data + (int64_t)field * V * 2);
     cx<T> reg[PER];
 #pragma unroll
@@ -212,18 +214,18 @@ __global__ void __launch_bounds__(NT) k_fx_cols(T *__restrict__ data, int64_t V,
       const T p2 = sxyz[c] + srow[n];
       const T w = p2 == zero ? zero : wscale / p2;
 #pragma unroll
-      for (int f = 0; f < 4; ++f) {
+      for (int f = 0; f < NF; ++f) {
         cx<T> &v = tile[f * TILE + n * P + c];
         v = scale(v, w);
       }
     }
     __syncthreads();
 #pragma unroll
-    for (int f = 0; f < 4; ++f) fx_axis<T, N, C, NT, true>(tile + f * TILE, tw, P, 1);
+    for (int f = 0; f < NF; ++f) fx_axis<T, N, C, NT, true>(tile + f * TILE, tw, P, 1);
   }
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
-    const int field = MODE == 2 ? f : (int)blockIdx.y;
+    const int field = MODE == 2 ? (int)blockIdx.y * FPB + f : (int)blockIdx.y;
     cx<T> *dst = reinterpret_cast<cx<T> *>(data + (int64_t)field * V * 2);
     for (int e = threadIdx.x; e < NEL; e += NT) {
       const int n = e / C, c = e % C;

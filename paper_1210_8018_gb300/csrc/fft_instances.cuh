@@ -19,14 +19,18 @@ template <typename T, bool INV> const void *plane(int n) {
     default: return (const void *)k_fx_plane<T, 64, 64, INV, kThreads>;
   }
 }
+// fields per block of the filter pass: one in float (small tiles), four otherwise (shared weights)
+template <typename T> constexpr int filter_fields_per_block() { return sizeof(T) == 4 ? 1 : 4; }
+
 template <typename T, int C, int MODE> const void *cols(int n) {
+  constexpr int F = filter_fields_per_block<T>();
   switch (n) {
-    case 8: return (const void *)k_fx_cols<T, 8, C, MODE, kThreads>;
-    case 16: return (const void *)k_fx_cols<T, 16, C, MODE, kThreads>;
-    case 24: return (const void *)k_fx_cols<T, 24, C, MODE, kThreads>;
-    case 32: return (const void *)k_fx_cols<T, 32, C, MODE, kThreads>;
-    case 48: return (const void *)k_fx_cols<T, 48, C, MODE, kThreads>;
-    default: return (const void *)k_fx_cols<T, 64, C, MODE, kThreads>;
+    case 8: return (const void *)k_fx_cols<T, 8, C, MODE, kThreads, F>;
+    case 16: return (const void *)k_fx_cols<T, 16, C, MODE, kThreads, F>;
+    case 24: return (const void *)k_fx_cols<T, 24, C, MODE, kThreads, F>;
+    case 32: return (const void *)k_fx_cols<T, 32, C, MODE, kThreads, F>;
+    case 48: return (const void *)k_fx_cols<T, 48, C, MODE, kThreads, F>;
+    default: return (const void *)k_fx_cols<T, 64, C, MODE, kThreads, F>;
   }
 }
 template <typename T, int C> const void *cols_mode(int mode, int n) {

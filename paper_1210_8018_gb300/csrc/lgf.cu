@@ -269,6 +269,7 @@ template <typename T> bool plan_fixed(lgf_ctx *ctx, State<T> &S) {
   const int64_t Nxy = (int64_t)Nx * Ny, Nxyz = Nxy * Nz;
   if (Nxy % C || Nxyz % C) return false;
   const size_t es = sizeof(cx<T>);
+  const int fields_per_filter_block = sizeof(T) == 4 ? 1 : 4;  // as in fft_instances.cuh
   auto plane = [&](int mode, int kid) {
     Pass p{};
     p.kind = 1;
@@ -293,7 +294,7 @@ template <typename T> bool plan_fixed(lgf_ctx *ctx, State<T> &S) {
     p.nblocks = ncb * nouter;
     p.twmu = twmu;
     p.threads = kFixedThreads;
-    p.smem = (size_t)((mode == 2 ? 4 : 1) * N * (C + 1) + N) * es;
+    p.smem = (size_t)((mode == 2 ? fields_per_filter_block : 1) * N * (C + 1) + N) * es;
     return p;
   };
   S.passes.clear();
@@ -438,7 +439,7 @@ template <typename T> lgf_status opt_in_smem(lgf_ctx *ctx, State<T> &S) {
 template <typename T> lgf_status setup_precision(lgf_ctx *ctx, State<T> &S) {
   const int64_t V = ctx->V;
   const size_t nb = (size_t)ctx->nb;
-  TRY(alloc(ctx, &S.U, nb * 4 * 9 * V * 2));
+  TRY(alloc(ctx, &S.U, nb * 4 * LinkStore<T>::planes * V * 2));
   TRY(alloc(ctx, &S.P, nb * 4 * V * 2));
   TRY(alloc(ctx, &S.G, nb * 9 * V * 2));
   if (!S.tw[0]) {
@@ -561,7 +562,7 @@ template <typename T> lgf_status launch_filter(lgf_ctx *ctx, State<T> &S, T *dat
       void *args[] = {&data, &V, &tb, &c, &check_active, (void *)&tk};
       CK(cudaLaunchKernel(fixed_kernel<FT>(p), grid, dim3(p.threads), args, p.smem, ctx->stream));
     } else {
-      dim3 grid(p.nblocks, p.mode == 2 ? 1 : 4, ctx->nb);
+      dim3 grid(p.nblocks, p.mode == 2 ? 4 / (sizeof(FT) == 4 ? 1 : 4) : 4, ctx->nb);
       int64_t V = ctx->V, rs = p.rstride, os = p.ostride;
       int ncb = p.ncb, twmu = p.twmu;
       FFTTables tb = S.tables;
@@ -672,15 +673,18 @@ lgf_status handover(lgf_ctx *ctx) {
 }
 
 // Timed wrappers of the layout conversions used by load and store.
+// nmat = 4: links (stored with LinkStore<T>::planes planes); nmat = 1: a site field of 9 planes.
 template <typename T> lgf_status to_planes(lgf_ctx *ctx, const double *src, T *dst, int nmat) {
   TRY(timed_begin(ctx, kid<T>(KID_TO_PLANES)));
-  k_aos_to_planes<T><<<grid1((int64_t)nmat * ctx->V, NT), NT, 0, ctx->stream>>>(src, dst, ctx->V, nmat);
+  const int np = nmat == 4 ? LinkStore<T>::planes : 9;
+  k_aos_to_planes<T><<<grid1((int64_t)nmat * ctx->V, NT), NT, 0, ctx->stream>>>(src, dst, ctx->V, nmat, np);
   CKL();
   return timed_end(ctx);
 }
 template <typename T> lgf_status from_planes(lgf_ctx *ctx, const T *src, double *dst, int nmat) {
   TRY(timed_begin(ctx, kid<T>(KID_FROM_PLANES)));
-  k_planes_to_aos<T><<<grid1((int64_t)nmat * ctx->V, NT), NT, 0, ctx->stream>>>(src, dst, ctx->V, nmat);
+  const int np = nmat == 4 ? LinkStore<T>::planes : 9;
+  k_planes_to_aos<T><<<grid1((int64_t)nmat * ctx->V, NT), NT, 0, ctx->stream>>>(src, dst, ctx->V, nmat, np);
   CKL();
   return timed_end(ctx);
 }
@@ -871,7 +875,7 @@ lgf_status lgf_load(lgf_ctx *ctx, const double *links, int precision) {
     ctx->stage = LGF_FP64;
   } else {
     TRY(setup_precision<float>(ctx, ctx->s32));
-    TRY(alloc(ctx, &ctx->Gacc, (size_t)ctx->nb * 9 * V * 2));
+    TRY(alloc(ctx, &ctx->Gacc, (size_t)ctx->nb * 6 * V * 2));
     if (precision == LGF_MIXED) {
       TRY(alloc(ctx, &ctx->U0, (size_t)ctx->nb * 4 * 9 * V * 2));
       TRY(to_planes<double>(ctx, src, ctx->U0, 4));
@@ -1020,7 +1024,7 @@ lgf_status lgf_measure(lgf_ctx *ctx, const double *links, double *theta, double 
   const int64_t V = ctx->V;
   const double *src = nullptr;
   TRY(input_ptr(ctx, links, (size_t)4 * V * 9 * 16, &ctx->staging, &ctx->staging_bytes, &src));
-  k_aos_to_planes<double><<<grid1(4 * V, NT), NT, 0, ctx->stream>>>(src, ctx->s64.U, V, 4);
+  k_aos_to_planes<double><<<grid1(4 * V, NT), NT, 0, ctx->stream>>>(src, ctx->s64.U, V, 4, 9);
   CKL();
   memset(&ctx->ctrl_host, 0, sizeof(Ctrl));
   TRY(write_ctrl(ctx));
@@ -1066,7 +1070,7 @@ template <typename T> static lgf_status unpack_field(lgf_ctx *ctx, State<T> &S, 
 template <typename T> static lgf_status step_delta(lgf_ctx *ctx, State<T> &S, const double *src, double *dst,
                                                    double *theta, double *F) {
   const int64_t V = ctx->V;
-  k_aos_to_planes<T><<<grid1(4 * V, NT), NT, 0, ctx->stream>>>(src, S.U, V, 4);
+  k_aos_to_planes<T><<<grid1(4 * V, NT), NT, 0, ctx->stream>>>(src, S.U, V, 4, LinkStore<T>::planes);
   CKL();
   memset(&ctx->ctrl_host, 0, sizeof(Ctrl));
   TRY(write_ctrl(ctx));
@@ -1136,7 +1140,7 @@ template <typename T> static lgf_status step_gauge(lgf_ctx *ctx, State<T> &S, co
   const int64_t V = ctx->V;
   TRY(pack_field<T>(ctx, S, src));
   TRY(launch_gauge<T>(ctx, S, alpha, 0));
-  k_planes_to_aos<T><<<grid1(V, NT), NT, 0, ctx->stream>>>(S.G, dst, V, 1);
+  k_planes_to_aos<T><<<grid1(V, NT), NT, 0, ctx->stream>>>(S.G, dst, V, 1, 9);
   CKL();
   return LGF_OK;
 }
@@ -1166,12 +1170,12 @@ extern "C" lgf_status lgf_gauge(lgf_ctx *ctx, const double *dtilde, double alpha
 template <typename T> static lgf_status step_update(lgf_ctx *ctx, State<T> &S, const double *lsrc, const double *gsrc,
                                                     double *dst) {
   const int64_t V = ctx->V;
-  k_aos_to_planes<T><<<grid1(4 * V, NT), NT, 0, ctx->stream>>>(lsrc, S.U, V, 4);
+  k_aos_to_planes<T><<<grid1(4 * V, NT), NT, 0, ctx->stream>>>(lsrc, S.U, V, 4, LinkStore<T>::planes);
   CKL();
-  k_aos_to_planes<T><<<grid1(V, NT), NT, 0, ctx->stream>>>(gsrc, S.G, V, 1);
+  k_aos_to_planes<T><<<grid1(V, NT), NT, 0, ctx->stream>>>(gsrc, S.G, V, 1, 9);
   CKL();
   TRY(launch_update<T>(ctx, S, 0));
-  k_planes_to_aos<T><<<grid1(4 * V, NT), NT, 0, ctx->stream>>>(S.U, dst, V, 4);
+  k_planes_to_aos<T><<<grid1(4 * V, NT), NT, 0, ctx->stream>>>(S.U, dst, V, 4, LinkStore<T>::planes);
   CKL();
   return LGF_OK;
 }

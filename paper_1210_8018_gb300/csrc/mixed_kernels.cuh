@@ -28,9 +28,9 @@ __global__ void __launch_bounds__(NT) k_update_fused_f32(float *__restrict__ U, 
   const int64_t V = L.V;
   {
     const int cfg = blockIdx.z;
-    U += (int64_t)cfg * 36 * V * 2;
+    U += (int64_t)cfg * 4 * link_plane_stride<float>(V);
     P += (int64_t)cfg * 4 * V * 2;
-    Gacc += (int64_t)cfg * 9 * V * 2;
+    Gacc += (int64_t)cfg * 6 * V * 2;
     ctrl += cfg;
   }
   if (!stage_active<float>(ctrl)) return;
@@ -41,18 +41,19 @@ __global__ void __launch_bounds__(NT) k_update_fused_f32(float *__restrict__ U, 
   site_coords(L, s, c);
   m3<float> gx, t, a;
   gauge_from_packed(P, V, s, half_alpha, gx);
+  // G(x) <- g(x) G(x), stored as rows 0 and 1 (like the float links)
 #pragma unroll
-  for (int e = 0; e < 9; ++e) a.e[e] = ld(Gacc, (int64_t)e * V + s);
-  mul(gx, a, t);
+  for (int e = 0; e < 6; ++e) a.e[e] = ld(Gacc, (int64_t)e * V + s);
+  complete_row2(a);
+  mul_rows01(gx, a, t);
 #pragma unroll
-  for (int e = 0; e < 9; ++e) st(Gacc, (int64_t)e * V + s, t.e[e]);
+  for (int e = 0; e < 6; ++e) st(Gacc, (int64_t)e * V + s, t.e[e]);
 #pragma unroll 1
   for (int mu = 0; mu < 4; ++mu) {
     const int64_t sf = site_fwd(L, s, mu, c[mu]);
-    float *plane = U + (int64_t)mu * 9 * V * 2;
+    float *plane = U + (int64_t)mu * link_plane_stride<float>(V);
     m3<float> u, gy;
-#pragma unroll
-    for (int e = 0; e < 9; ++e) u.e[e] = ld(plane, (int64_t)e * V + s);
+    load_link(plane, V, s, u);
     gauge_from_packed(P, V, sf, half_alpha, gy);
     mul_rows01(gx, u, t);
     mul_adj_rows01(t, gy, u);
@@ -62,12 +63,9 @@ __global__ void __launch_bounds__(NT) k_update_fused_f32(float *__restrict__ U, 
       for (int e = 0; e < 6; ++e) d.e[e] = {(double)u.e[e].r, (double)u.e[e].i};
       reunitarize(d);
 #pragma unroll
-      for (int e = 0; e < 9; ++e) u.e[e] = {(float)d.e[e].r, (float)d.e[e].i};
-    } else {
-      complete_row2(u);
+      for (int e = 0; e < 6; ++e) u.e[e] = {(float)d.e[e].r, (float)d.e[e].i};
     }
-#pragma unroll
-    for (int e = 0; e < 9; ++e) st(plane, (int64_t)e * V + s, u.e[e]);
+    store_link(plane, V, s, u);
   }
 }
 
@@ -78,8 +76,9 @@ __global__ void __launch_bounds__(NT) k_gacc_to_double(const float *__restrict__
   const int64_t s = (int64_t)blockIdx.x * NT + threadIdx.x;
   if (s >= V) return;
   m3<double> m;
+  // rows 0 and 1 of G; the projection rebuilds row 2
 #pragma unroll
-  for (int e = 0; e < 9; ++e) {
+  for (int e = 0; e < 6; ++e) {
     const cx<float> v = ldg(Gacc, (int64_t)e * V + s);
     m.e[e] = {(double)v.r, (double)v.i};
   }
@@ -122,7 +121,7 @@ __global__ void k_set_identity(float *__restrict__ Gacc, int64_t V) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= V) return;
 #pragma unroll
-  for (int e = 0; e < 9; ++e) st(Gacc, (int64_t)e * V + s, mkc((e % 4 == 0) ? 1.0f : 0.0f, 0.0f));
+  for (int e = 0; e < 6; ++e) st(Gacc, (int64_t)e * V + s, mkc((e % 4 == 0) ? 1.0f : 0.0f, 0.0f));  // rows 0-1
 }
 
 }  // namespace lgf

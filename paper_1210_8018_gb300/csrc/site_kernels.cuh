@@ -3,7 +3,9 @@
 // of g (Eq. 2 to first order, then projection to SU(3)) and the gauge update of the links.
 //
 // Working layout (structure of arrays, one plane of V complex numbers per matrix element):
-//   links  U[(mu*9 + e)*V + s]   mu = 0..3, e = 3*row + col
+//   links  U[(mu*P + e)*V + s]   mu = 0..3, e = 3*row + col; P = 9 planes in double, P = 6 in float
+//          (rows 0 and 1 only: the float stage is bound by memory traffic, so row 2 is rebuilt as
+//          conj(row0 x row1) when a link is loaded -- the paper's "12 real" storage, Table 1)
 //   g      G[e*V + s]
 //   packed Delta (and Delta-tilde) P[f*V + s], f = 0..3:
 //     P0 = Delta_01, P1 = Delta_02, P2 = Delta_12, P3 = Im Delta_00 + i Im Delta_11.
@@ -43,6 +45,28 @@ struct Ctrl {
 __device__ __forceinline__ void count_run(const Ctrl *ctrl, int tkid) {
   if (ctrl->ran && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0)
     atomicAdd(ctrl->ran + tkid, 1u);
+}
+
+// Link storage: planes per link and the load/store of one link.
+template <typename T> struct LinkStore {
+  static constexpr int planes = 9;
+};
+template <> struct LinkStore<float> {
+  static constexpr int planes = 6;
+};
+template <typename T> __device__ __forceinline__ void load_link(const T *plane, int64_t V, int64_t s, m3<T> &u) {
+#pragma unroll
+  for (int e = 0; e < LinkStore<T>::planes; ++e) u.e[e] = ldg(plane, (int64_t)e * V + s);
+  if constexpr (LinkStore<T>::planes == 6) complete_row2(u);
+}
+// Store a link whose rows 0 and 1 are valid (row 2 is completed here when it is stored).
+template <typename T> __device__ __forceinline__ void store_link(T *plane, int64_t V, int64_t s, m3<T> &u) {
+  if constexpr (LinkStore<T>::planes == 9) complete_row2(u);
+#pragma unroll
+  for (int e = 0; e < LinkStore<T>::planes; ++e) st(plane, (int64_t)e * V + s, u.e[e]);
+}
+template <typename T> __device__ __forceinline__ int64_t link_plane_stride(int64_t V) {
+  return (int64_t)LinkStore<T>::planes * V * 2;
 }
 
 // Batched launches: blockIdx.z selects one configuration of a group of equal-shape lattices whose
@@ -156,20 +180,16 @@ __device__ __forceinline__ void reduce_and_finalize(double th, double f, double 
 // ---------------------------------------------------------------------------------------------
 constexpr int kSitesPerThread = 4;
 
-template <typename T>
-__device__ __forceinline__ void accumulate_link(const T *plane, int64_t V, int64_t s, T sign, T acc[9]) {
-  const cx<T> u00 = ldg(plane, s), u01 = ldg(plane, V + s), u02 = ldg(plane, 2 * V + s);
-  const cx<T> u10 = ldg(plane, 3 * V + s), u11 = ldg(plane, 4 * V + s), u12 = ldg(plane, 5 * V + s);
-  const cx<T> u20 = ldg(plane, 6 * V + s), u21 = ldg(plane, 7 * V + s), u22 = ldg(plane, 8 * V + s);
-  acc[0] = fma(sign, u01.r - u10.r, acc[0]);
-  acc[1] = fma(sign, u01.i + u10.i, acc[1]);
-  acc[2] = fma(sign, u02.r - u20.r, acc[2]);
-  acc[3] = fma(sign, u02.i + u20.i, acc[3]);
-  acc[4] = fma(sign, u12.r - u21.r, acc[4]);
-  acc[5] = fma(sign, u12.i + u21.i, acc[5]);
-  acc[6] = fma(sign, u00.i, acc[6]);
-  acc[7] = fma(sign, u11.i, acc[7]);
-  acc[8] = fma(sign, u22.i, acc[8]);
+template <typename T> __device__ __forceinline__ void accumulate_link(const m3<T> &u, T sign, T acc[9]) {
+  acc[0] = fma(sign, u.e[1].r - u.e[3].r, acc[0]);
+  acc[1] = fma(sign, u.e[1].i + u.e[3].i, acc[1]);
+  acc[2] = fma(sign, u.e[2].r - u.e[6].r, acc[2]);
+  acc[3] = fma(sign, u.e[2].i + u.e[6].i, acc[3]);
+  acc[4] = fma(sign, u.e[5].r - u.e[7].r, acc[4]);
+  acc[5] = fma(sign, u.e[5].i + u.e[7].i, acc[5]);
+  acc[6] = fma(sign, u.e[0].i, acc[6]);
+  acc[7] = fma(sign, u.e[4].i, acc[7]);
+  acc[8] = fma(sign, u.e[8].i, acc[8]);
 }
 
 // PT is the type of the packed output (T, or float when a double stage feeds a float FFT).
@@ -179,7 +199,7 @@ __global__ void __launch_bounds__(NT) k_delta(const T *__restrict__ U, PT *__res
   const int64_t V = L.V;
   {
     const int cfg = blockIdx.z;
-    U += (int64_t)cfg * 36 * V * 2;
+    U += (int64_t)cfg * 4 * link_plane_stride<T>(V);
     P += (int64_t)cfg * 4 * V * 2;
     partials += (int64_t)cfg * 2 * gridDim.x;
     ctrl += cfg;
@@ -199,10 +219,13 @@ __global__ void __launch_bounds__(NT) k_delta(const T *__restrict__ U, PT *__res
     T fs = 0;
 #pragma unroll
     for (int mu = 0; mu < 4; ++mu) {
-      const T *plane = U + (int64_t)mu * 9 * V * 2;
-      accumulate_link(plane, V, site_back(L, s, mu, c[mu]), (T)1, acc);  // U_mu(x - mu)
-      accumulate_link(plane, V, s, (T)-1, acc);                          // - U_mu(x)
-      fs += ldg(plane, s).r + ldg(plane, 4 * V + s).r + ldg(plane, 8 * V + s).r;  // Re Tr U_mu(x)
+      const T *plane = U + (int64_t)mu * link_plane_stride<T>(V);
+      m3<T> u;
+      load_link(plane, V, site_back(L, s, mu, c[mu]), u);  // U_mu(x - mu)
+      accumulate_link(u, (T)1, acc);
+      load_link(plane, V, s, u);  // - U_mu(x)
+      accumulate_link(u, (T)-1, acc);
+      fs += u.e[0].r + u.e[4].r + u.e[8].r;  // Re Tr U_mu(x)
     }
     // Delta_ij = acc (off-diagonal), Delta_ii = 2i (Im B_ii - mean)
     const T m = (acc[6] + acc[7] + acc[8]) / (T)3;
@@ -273,7 +296,7 @@ __global__ void __launch_bounds__(NT) k_update(T *__restrict__ U, const T *__res
   const int64_t V = L.V;
   {
     const int cfg = blockIdx.z;
-    U += (int64_t)cfg * 36 * V * 2;
+    U += (int64_t)cfg * 4 * link_plane_stride<T>(V);
     G += (int64_t)cfg * 9 * V * 2;
     ctrl += cfg;
   }
@@ -289,19 +312,15 @@ __global__ void __launch_bounds__(NT) k_update(T *__restrict__ U, const T *__res
 #pragma unroll 1
   for (int mu = 0; mu < 4; ++mu) {
     const int64_t sf = site_fwd(L, s, mu, c[mu]);
-    T *plane = U + (int64_t)mu * 9 * V * 2;
+    T *plane = U + (int64_t)mu * link_plane_stride<T>(V);
     m3<T> u, gy, t;
+    load_link(plane, V, s, u);
 #pragma unroll
-    for (int e = 0; e < 9; ++e) {
-      u.e[e] = ld(plane, (int64_t)e * V + s);
-      gy.e[e] = ldg(G, (int64_t)e * V + sf);
-    }
+    for (int e = 0; e < 9; ++e) gy.e[e] = ldg(G, (int64_t)e * V + sf);
     // rows 0 and 1 of g(x) U g^+(x+mu) by products, row 2 = conj(row0 x row1) (the result is in SU(3))
     mul_rows01(gx, u, t);
     mul_adj_rows01(t, gy, u);
-    complete_row2(u);
-#pragma unroll
-    for (int e = 0; e < 9; ++e) st(plane, (int64_t)e * V + s, u.e[e]);
+    store_link(plane, V, s, u);
   }
 }
 
@@ -309,31 +328,30 @@ __global__ void __launch_bounds__(NT) k_update(T *__restrict__ U, const T *__res
 // Layout conversions between the caller's array-of-structures links / site fields (double) and the
 // working planes (T). These run once per load/store, not in the loop.
 // ---------------------------------------------------------------------------------------------
+// A: nmat*V matrices of 9 complex; Pl: planes [(m*np + e)*V + s], np = 9, or 6 (rows 0-1 of links)
 template <typename T>
-__global__ void k_aos_to_planes(const double *__restrict__ A, T *__restrict__ Pl, int64_t V, int nmat) {
-  // A: nmat*V matrices of 9 complex; Pl: planes [(m*9 + e)*V + s]
+__global__ void k_aos_to_planes(const double *__restrict__ A, T *__restrict__ Pl, int64_t V, int nmat, int np) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)nmat * V) return;
   const int64_t m = idx / V, s = idx - m * V;
   const double2 *src = reinterpret_cast<const double2 *>(A) + idx * 9;
-#pragma unroll
-  for (int e = 0; e < 9; ++e) {
+  for (int e = 0; e < np; ++e) {
     const double2 v = src[e];
-    st(Pl, (m * 9 + e) * V + s, mkc((T)v.x, (T)v.y));
+    st(Pl, (m * np + e) * V + s, mkc((T)v.x, (T)v.y));
   }
 }
 
 template <typename T>
-__global__ void k_planes_to_aos(const T *__restrict__ Pl, double *__restrict__ A, int64_t V, int nmat) {
+__global__ void k_planes_to_aos(const T *__restrict__ Pl, double *__restrict__ A, int64_t V, int nmat, int np) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)nmat * V) return;
   const int64_t m = idx / V, s = idx - m * V;
   double2 *dst = reinterpret_cast<double2 *>(A) + idx * 9;
+  m3<T> u;
+  for (int e = 0; e < np; ++e) u.e[e] = ld(Pl, (m * np + e) * V + s);
+  if (np == 6) complete_row2(u);
 #pragma unroll
-  for (int e = 0; e < 9; ++e) {
-    const cx<T> v = ld(Pl, (m * 9 + e) * V + s);
-    dst[e] = make_double2((double)v.r, (double)v.i);
-  }
+  for (int e = 0; e < 9; ++e) dst[e] = make_double2((double)u.e[e].r, (double)u.e[e].i);
 }
 
 // Full site matrices (AoS double) <-> packed anti-Hermitian traceless fields (planes of PT).

@@ -127,3 +127,20 @@ def test_adam_drives_theta_down(env):
     res = lgf.adam_fix(torch.from_numpy(U).cuda(), target=1e-10, max_steps=4000)
     assert res["theta"] <= 1e-10, res
     assert res["F"] > res["F0"]
+
+
+def test_sgd_on_preconditioned_gradient_reproduces_algorithm_1(env):
+    """torch.optim.SGD on the Fourier-preconditioned gradient with lr = 24 alpha V and re-basing after
+    each step is Algorithm 1's step (exponential instead of first order): it converges like the
+    library's own fix."""
+    torch, lgf = env
+    dims = (8, 8, 8, 8)
+    V = 8 ** 4
+    U = synth.config(dims, 1, 0.3)
+    with lgf.Lattice(dims) as lat:
+        r_ref = lat.fix(U.copy(), 0.08, 1e-10, "fp64")
+    res = lgf.adam_fix(torch.from_numpy(U).cuda(), target=1e-10, optimizer="sgd", precondition=True,
+                       lr=24 * 0.08 * V, rebase_every=1, check_every=1, max_steps=200)
+    assert res["theta"] <= 1e-10
+    assert abs(res["steps"] - r_ref["iters"]) <= 3, (res["steps"], r_ref["iters"])
+    assert abs(res["F"] - r_ref["F"]) < 1e-8
