@@ -38,7 +38,8 @@ UNIT = "site-iterations/s"
 
 # Nominal FP64 rate derived from the unit counts and clock: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop
 # x 2.07 GHz = 1.259 TFLOP/s (GB300 FP64 is 1.25 TFLOP/s nominal).
-FP64_FLOP_PER_CLK = 152 * 2 * 2
+FP64_FLOP_PER_CLK = 152 * 2 * 2      # 152 SMs x 2 DFMA per clock x 2 flop
+FP32_OPS_PER_CLK = 152 * 128         # 152 SMs x 128 FP32 lanes (one FADD, FMUL or FFMA each per clock)
 
 
 def peaks():
@@ -50,8 +51,10 @@ def peaks():
 
 
 def algorithmic(kernel, dims):
-    """Algorithmic bytes and flops per launch of each kernel (each datum counted once).
-    es = bytes per complex number; flops counted in the kernel's own precision."""
+    """Algorithmic bytes and arithmetic per launch of each kernel (each datum counted once).
+    es = bytes per complex number. The arithmetic is (count, kind): kind "fp64" counts FP64 flops (FMA = 2),
+    kind "fp32" counts FP32-pipe operations (FADD, FMUL, FFMA = 1 each), None when the kernel is modelled by
+    its bytes only."""
     V = int(np.prod(dims))
     name, prec = kernel.rsplit(".", 1)
     es = 16 if prec == "f64" else 8
@@ -71,9 +74,11 @@ def algorithmic(kernel, dims):
         "fft_t_filter": (8 * es, 4 * (2 * 5 * lg["t"] + 6)),
         # packed Delta-tilde read, g written
         "gauge_g": ((4 + 9) * es, 160),
-        # links read and written, g read (neighbours are the same data); per link rows 0-1 of
-        # g U (18 complex MACs) and of (g U) g^+ (18), row 2 by a cross product: 168 FMA = 336 flop
-        "gauge_update": ((4 * lp * 2 + 9) * es, 4 * 336),
+        # links read and written, g read (neighbours are the same data). Double: the small-step form,
+        # which every warp of the double stage takes: per link two 3x3 complex products in double-float,
+        # 9 x 3 x 4 x 2 = 216 real multiply-accumulates of 12 FP32 operations each (Dot2 step). Float
+        # (plain FP32 schedule): rows 0-1 of g U and of (g U) g^+, row 2 by a cross product, 336 flop.
+        "gauge_update": ((4 * lp * 2 + 9) * es, 4 * 216 * 12 if prec == "f64" else 4 * 336),
         # float stage: links read and written, G read and written (rows 0-1), packed Delta-tilde read (g is
         # rebuilt in registers); the _reunit variant also projects the new links in double precision
         "gauge_update_fused": ((4 * lp * 2 + 12 + 4) * es, 0),
@@ -85,7 +90,11 @@ def algorithmic(kernel, dims):
         "set_identity": (6 * 8, 0),
     }
     b, f = table[name]
-    return b * V, f * V, prec
+    if prec == "f64":
+        kind = {"gauge_update": "fp32", "handover_transform": "fp64", "gacc_to_double": "fp64"}.get(name)
+    else:
+        kind = "fp64" if name == "gauge_update_fused_reunit" else None
+    return b * V, (f * V if kind else 0), kind
 
 
 class ClockSampler:
@@ -447,27 +456,30 @@ def main():
     # roofline of every kernel; the dominant kernel (largest share of the timed steps) is reported
     hbm, sm_max, which = peaks()
     clocks = clk.summary()
-    fp64_peak = FP64_FLOP_PER_CLK * (clocks["sm_mhz"] or sm_max) * 1e6
+    clk_hz = (clocks["sm_mhz"] or sm_max) * 1e6
+    alu_peak = {"fp64": (FP64_FLOP_PER_CLK * clk_hz, "TFLOP/s", "152 SMs x 4 FP64 flop/clk"),
+                "fp32": (FP32_OPS_PER_CLK * clk_hz, "Tops/s (FP32-pipe operations)", "152 SMs x 128 FP32 ops/clk")}
     kernels = {}
     total_ms = sum(v[1] for v in ktimes.values())
     for name, (n, kms) in ktimes.items():
-        b, f, prec = algorithmic(name, dims)
+        b, f, kind = algorithmic(name, dims)
         per = kms / n / 1e3
         gbs = b / per / 1e9
         d = {"launches": n, "ms_total": round(kms, 3), "share": round(kms / total_ms, 4),
              "ms_per_launch": round(kms / n, 4), "GB_s": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4)}
-        if prec == "f64" and f > 0:
-            d["fp64_tflops"] = round(f / per / 1e12, 4)
-            d["fp64_frac"] = round(f / per / fp64_peak, 4)
+        if kind:
+            d["alu_kind"] = kind
+            d["alu_frac"] = round(f / per / alu_peak[kind][0], 4)
         kernels[name] = d
     dom = max(kernels, key=lambda k: kernels[k]["ms_total"])
     dk = kernels[dom]
-    b, f, prec = algorithmic(dom, dims)
+    b, f, kind = algorithmic(dom, dims)
     per = dk["ms_per_launch"] / 1e3
-    if prec == "f64" and dk.get("fp64_frac", 0) > dk["hbm_frac"]:
-        roof = {"bound": "alu", "achieved": round(f / per / 1e12, 4), "peak": round(fp64_peak / 1e12, 4),
-                "unit": "TFLOP/s", "frac": round(f / per / fp64_peak, 4), "traffic": None,
-                "kernel": dom, "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x median SM clock"}
+    if kind and dk["alu_frac"] > dk["hbm_frac"]:
+        pk, unit, src = alu_peak[kind]
+        roof = {"bound": "alu", "achieved": round(f / per / 1e12, 4), "peak": round(pk / 1e12, 4),
+                "unit": unit, "frac": round(f / per / pk, 4), "traffic": None,
+                "kernel": dom, "peak_source": "derived: %s x median SM clock under load" % src}
     else:
         roof = {"bound": "hbm", "achieved": round(b / per / 1e9, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(b / per / 1e9 / hbm, 4), "traffic": None, "kernel": dom,

@@ -69,7 +69,14 @@ void lgf_default_options(lgf_options *opt);
 
 /* Create a context for an Nx x Ny x Nz x Nt lattice on the current CUDA device. Every extent must be
  * >= 2 and a product of the primes 2, 3 and 5, and at most 1024. Device memory is allocated lazily by
- * the first call that needs it. Returns LGF_EINVAL for unsupported extents, LGF_ECUDA if no device. */
+ * the first call that needs it. Returns LGF_EINVAL for unsupported extents, LGF_ECUDA if no device.
+ * Environment switches read here, each selecting an equivalent form of a step (all pass the same
+ * tests): LGF_GENERIC_FFT=1 uses the generic FFT passes for every extent; LGF_FFT_NATIVE_F64=1 runs
+ * the Fourier filter of the double path in IEEE double instead of double-float; and LGF_SMALL_STEP=0
+ * turns off the small-step forms of the double path, which by default apply per warp where the step
+ * is small: g = 1 + a formed in double-float when every |(alpha/2) Delta-tilde| < 2^-8, and the update
+ * U + [a U + (U + a U) b^+] (a = g(x) - 1, b = g(x+mu) - 1) with the bracket in double-float when
+ * every |a|, |b| < 2^-7. Their errors are at the level of the FP64 rounding of the plain forms. */
 lgf_status lgf_create(int Nx, int Ny, int Nz, int Nt, lgf_ctx **out);
 
 /* Release every resource of the context (NULL is accepted). */

@@ -119,4 +119,47 @@ template <> struct Conv<df64, float> {
 };
 template <typename D, typename S> __device__ __forceinline__ D convert(S s) { return Conv<D, S>::f(s); }
 
+// double -> double-float without an integer-to-float conversion instruction: hi is the truncation to
+// the top 24 significant bits (exact); the remaining 29 bits are rounded to 23 and placed in the
+// mantissa field of a float whose implicit leading 1 is then subtracted (exact by Sterbenz's lemma; a
+// carry out of the rounded field moves into the exponent, which gives the right value). The pair
+// (hi, lo) is not renormalised: |lo| <= ulp(hi), and |hi + lo - d| <= 2^-47 |d|. Magnitudes below
+// 2^-100 give 0 and the input must be finite; callers use it on matrix elements of magnitude <= 1.
+__device__ __forceinline__ df64 df64_split_fast(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned hi32 = (unsigned)(b >> 32), lo32 = (unsigned)b;
+  const int ed = (int)((hi32 >> 20) & 0x7FF);
+  const unsigned sign = hi32 & 0x80000000u;
+  const int ef = ed - 896;  // float exponent field of hi
+  const int E = ed - 919;   // float exponent field whose mantissa unit is 2^(e - 46)
+  if (E < 1) return {0.f, 0.f};
+  const float hi = __uint_as_float(sign | ((unsigned)ef << 23) | ((hi32 & 0xFFFFFu) << 3) | (lo32 >> 29));
+  const unsigned m = ((lo32 & 0x1FFFFFFFu) + 32u) >> 6;  // the remaining 29 bits rounded to 23 (may be 2^23)
+  const unsigned base = sign | ((unsigned)E << 23);
+  const float lo = __fsub_rn(__uint_as_float(base + m), __uint_as_float(base));
+  return {hi, lo};
+}
+
+// Compensated accumulation of products of double-float numbers: the scheme of Ogita, Rump and Oishi,
+// "Accurate sum and dot product" (2005, Dot2), applied to double-float operands. s collects the float
+// sum of the leading products through TwoSum; c collects the exact product errors (FMA), the cross
+// terms hi*lo and the TwoSum errors. The result s + c has an absolute error of a few 2^-48 times the
+// sum of the magnitudes of the products.
+struct dfacc {
+  float s, c;
+};
+__device__ __forceinline__ dfacc dfacc_from(df64 x) { return {x.hi, x.lo}; }
+__device__ __forceinline__ void dfacc_mac(dfacc &a, df64 x, df64 y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  const df64 t = two_sum(a.s, p);
+  a.s = t.hi;
+  a.c = __fadd_rn(a.c, __fadd_rn(t.lo, e));
+}
+// the same with the product negated
+__device__ __forceinline__ void dfacc_msub(dfacc &a, df64 x, df64 y) { dfacc_mac(a, df64{-x.hi, -x.lo}, y); }
+__device__ __forceinline__ df64 dfacc_result(dfacc a) { return two_sum(a.s, a.c); }
+
 }  // namespace lgf

@@ -2,6 +2,8 @@
 // type in their own translation units (fft_float.cu, fft_double.cu, fft_df64_*.cu) so that the library
 // compiles in parallel; the host code launches them through these pointers with cudaLaunchKernel.
 #pragma once
+#include <type_traits>
+
 #include "df64.cuh"
 
 namespace lgf {
@@ -11,5 +13,9 @@ namespace lgf {
 template <typename FT> const void *fft_fixed_kernel(int kind, int mode, int N, int C);
 // Generic pass (fft.cuh, k_fft_pass).
 template <typename FT> const void *fft_generic_kernel();
+
+// Packed fields per block of the column pass with the filter (kind 2, mode 2): one (small tiles, more
+// resident blocks), except in IEEE double, where four fields share the weights of the FP64 pipe.
+template <typename FT> constexpr int filter_fields_per_block() { return std::is_same<FT, double>::value ? 4 : 1; }
 
 }  // namespace lgf

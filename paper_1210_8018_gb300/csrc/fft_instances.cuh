@@ -19,9 +19,6 @@ template <typename T, bool INV> const void *plane(int n) {
     default: return (const void *)k_fx_plane<T, 64, 64, INV, kThreads>;
   }
 }
-// fields per block of the filter pass: one in float (small tiles), four otherwise (shared weights)
-template <typename T> constexpr int filter_fields_per_block() { return sizeof(T) == 4 ? 1 : 4; }
-
 template <typename T, int C, int MODE> const void *cols(int n) {
   constexpr int F = filter_fields_per_block<T>();
   switch (n) {

@@ -29,6 +29,9 @@ using namespace lgf;
 namespace {
 
 constexpr int NT = 256;  // threads per block of the per-site kernels
+// threads per block of the double gauge update: its links and g(x+mu) are staged in 72 KB of shared
+// memory per block (three blocks per SM)
+constexpr int NT_UPDATE64 = 128;
 
 enum KernelId {
   KID_DELTA = 0,
@@ -127,6 +130,7 @@ struct lgf_ctx {
   int since_reunit = 0;
   bool generic_fft = false;  // force the generic FFT passes (tests compare the two families)
   bool fft_df64 = true;      // double state: Fourier filter in df64 (LGF_FFT_NATIVE_F64=1: IEEE double)
+  bool small_step = true;    // double g and update: small-step forms where they apply (LGF_SMALL_STEP=0: never)
   int fixed_cols[2] = {0, 0};  // column width of the specialised passes (double, float); 0 = default
   double prev_theta = 0;  // theta and iteration count at the previous chunk boundary
   int prev_iters = 0;
@@ -269,7 +273,8 @@ template <typename T> bool plan_fixed(lgf_ctx *ctx, State<T> &S) {
   const int64_t Nxy = (int64_t)Nx * Ny, Nxyz = Nxy * Nz;
   if (Nxy % C || Nxyz % C) return false;
   const size_t es = sizeof(cx<T>);
-  const int fields_per_filter_block = sizeof(T) == 4 ? 1 : 4;  // as in fft_instances.cuh
+  // filter_fields_per_block<FT>() of the FFT type FT of this state
+  const int fields_per_filter_block = (sizeof(T) == 8 && !ctx->fft_df64) ? filter_fields_per_block<double>() : 1;
   auto plane = [&](int mode, int kid) {
     Pass p{};
     p.kind = 1;
@@ -463,6 +468,12 @@ template <typename T> lgf_status setup_precision(lgf_ctx *ctx, State<T> &S) {
     }
     S.tables.wscale = ctx->wscale;
     TRY(opt_in_smem<T>(ctx, S));
+    if constexpr (std::is_same<T, double>::value) {
+      CK(cudaFuncSetAttribute(k_update<double, NT_UPDATE64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)update_smem_bytes<NT_UPDATE64>()));
+      CK(cudaFuncSetAttribute(k_update<double, NT_UPDATE64>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                              (int)cudaSharedmemCarveoutMaxShared));
+    }
   }
   return LGF_OK;
 }
@@ -562,7 +573,7 @@ template <typename T> lgf_status launch_filter(lgf_ctx *ctx, State<T> &S, T *dat
       void *args[] = {&data, &V, &tb, &c, &check_active, (void *)&tk};
       CK(cudaLaunchKernel(fixed_kernel<FT>(p), grid, dim3(p.threads), args, p.smem, ctx->stream));
     } else {
-      dim3 grid(p.nblocks, p.mode == 2 ? 4 / (sizeof(FT) == 4 ? 1 : 4) : 4, ctx->nb);
+      dim3 grid(p.nblocks, p.mode == 2 ? 4 / filter_fields_per_block<FT>() : 4, ctx->nb);
       int64_t V = ctx->V, rs = p.rstride, os = p.ostride;
       int ncb = p.ncb, twmu = p.twmu;
       FFTTables tb = S.tables;
@@ -582,7 +593,8 @@ template <typename T> lgf_status launch_gauge(lgf_ctx *ctx, State<T> &S, double 
   TRY(with_fft_type<T>(ctx, [&](auto tag) -> lgf_status {
     using FT = decltype(tag);
     k_gauge<T, NT, FT><<<dim3(grid1(ctx->V, NT), 1, ctx->nb), NT, 0, ctx->stream>>>(
-        reinterpret_cast<const FT *>(S.P), S.G, (T)(0.5 * alpha), ctx->V, ctx->ctrl, check_active, kid<T>(KID_GAUGE));
+        reinterpret_cast<const FT *>(S.P), S.G, (T)(0.5 * alpha), ctx->V, ctx->ctrl, check_active, kid<T>(KID_GAUGE),
+        ctx->small_step ? 1 : 0);
     CKL();
     return LGF_OK;
   }));
@@ -591,8 +603,14 @@ template <typename T> lgf_status launch_gauge(lgf_ctx *ctx, State<T> &S, double 
 
 template <typename T> lgf_status launch_update(lgf_ctx *ctx, State<T> &S, int check_active) {
   TRY(timed_begin(ctx, kid<T>(KID_UPDATE)));
-  k_update<T, NT><<<dim3(grid1(ctx->V, NT), 1, ctx->nb), NT, 0, ctx->stream>>>(S.U, S.G, ctx->L, ctx->ctrl, check_active,
-                                                             kid<T>(KID_UPDATE));
+  if constexpr (std::is_same<T, double>::value) {
+    k_update<double, NT_UPDATE64><<<dim3(grid1(ctx->V, NT_UPDATE64), 1, ctx->nb), NT_UPDATE64,
+                                    update_smem_bytes<NT_UPDATE64>(), ctx->stream>>>(
+        S.U, S.G, ctx->L, ctx->ctrl, check_active, kid<T>(KID_UPDATE), ctx->small_step ? 1 : 0);
+  } else {
+    k_update<T, NT><<<dim3(grid1(ctx->V, NT), 1, ctx->nb), NT, 0, ctx->stream>>>(S.U, S.G, ctx->L, ctx->ctrl,
+                                                                               check_active, kid<T>(KID_UPDATE), 0);
+  }
   CKL();
   return timed_end(ctx);
 }
@@ -618,7 +636,7 @@ lgf_status launch_iteration_fft32(lgf_ctx *ctx, double alpha) {
   TRY(launch_filter<float>(ctx, ctx->s32, ctx->s32.P, 2));
   TRY(timed_begin(ctx, kid<double>(KID_GAUGE)));
   k_gauge<double, NT, float><<<dim3(grid1(ctx->V, NT), 1, ctx->nb), NT, 0, ctx->stream>>>(
-      ctx->s32.P, ctx->s64.G, 0.5 * alpha, ctx->V, ctx->ctrl, 1, kid<double>(KID_GAUGE));
+      ctx->s32.P, ctx->s64.G, 0.5 * alpha, ctx->V, ctx->ctrl, 1, kid<double>(KID_GAUGE), ctx->small_step ? 1 : 0);
   CKL();
   TRY(timed_end(ctx));
   TRY(launch_update<double>(ctx, ctx->s64, 1));
@@ -777,6 +795,8 @@ static lgf_status create_ctx(const int n[4], int nb, lgf_ctx **out) {
     ctx->generic_fft = g && g[0] == '1';
     const char *nf = std::getenv("LGF_FFT_NATIVE_F64");
     ctx->fft_df64 = !(nf && nf[0] == '1');
+    const char *ss = std::getenv("LGF_SMALL_STEP");
+    ctx->small_step = !(ss && ss[0] == '0');
   }
   cudaDeviceGetAttribute(&ctx->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
   // p^2 tables (position -> 4 sin^2(pi k / N)) and the filter scale p^2_max / V
@@ -1074,8 +1094,17 @@ template <typename T> static lgf_status step_delta(lgf_ctx *ctx, State<T> &S, co
   CKL();
   memset(&ctx->ctrl_host, 0, sizeof(Ctrl));
   TRY(write_ctrl(ctx));
-  TRY(launch_delta<T>(ctx, S, 0, 0));
-  TRY(unpack_field<T>(ctx, S, dst));
+  if constexpr (std::is_same<T, double>::value) {
+    // the caller gets Delta in full FP64: pack it as double, not as the type of the double path's FFT
+    k_delta<double, NT, double><<<dim3(ctx->nblocks_site, 1, 1), NT, 0, ctx->stream>>>(
+        S.U, S.P, ctx->partials, ctx->ctrl, ctx->L, 0, 0, kid<T>(KID_DELTA));
+    CKL();
+    k_unpack_antiherm<double><<<grid1(V, NT), NT, 0, ctx->stream>>>(S.P, dst, V);
+    CKL();
+  } else {
+    TRY(launch_delta<T>(ctx, S, 0, 0));
+    TRY(unpack_field<T>(ctx, S, dst));
+  }
   TRY(read_ctrl(ctx));
   if (theta) *theta = ctx->ctrl_host.theta;
   if (F) *F = ctx->ctrl_host.F;
@@ -1138,8 +1167,17 @@ extern "C" lgf_status lgf_filter(lgf_ctx *ctx, const double *delta, double *dtil
 template <typename T> static lgf_status step_gauge(lgf_ctx *ctx, State<T> &S, const double *src, double alpha,
                                                    double *dst) {
   const int64_t V = ctx->V;
-  TRY(pack_field<T>(ctx, S, src));
-  TRY(launch_gauge<T>(ctx, S, alpha, 0));
+  if constexpr (std::is_same<T, double>::value) {
+    // Delta-tilde from the caller is taken in full FP64 (packed as double)
+    k_pack_antiherm<double><<<grid1(V, NT), NT, 0, ctx->stream>>>(src, S.P, V);
+    CKL();
+    k_gauge<double, NT, double><<<dim3(grid1(V, NT), 1, 1), NT, 0, ctx->stream>>>(
+        S.P, S.G, 0.5 * alpha, V, ctx->ctrl, 0, kid<T>(KID_GAUGE), ctx->small_step ? 1 : 0);
+    CKL();
+  } else {
+    TRY(pack_field<T>(ctx, S, src));
+    TRY(launch_gauge<T>(ctx, S, alpha, 0));
+  }
   k_planes_to_aos<T><<<grid1(V, NT), NT, 0, ctx->stream>>>(S.G, dst, V, 1, 9);
   CKL();
   return LGF_OK;

@@ -192,6 +192,38 @@ template <typename T> __device__ __forceinline__ void accumulate_link(const m3<T
   acc[8] = fma(sign, u.e[8].i, acc[8]);
 }
 
+// The double path accumulates Delta in 64-bit fixed point with 56 fractional bits: Delta is a sum of
+// eight O(1) link terms whose result is small, so integer sums give it exactly (up to the 2^-56
+// quantisation of link entries below 2^-4, far below the FP64 rounding of the terms), and the integer
+// pipe runs at 32 times the FP64 rate on this GPU. Converted back to double once, the result is at least
+// as accurate as the FP64 sum. Entries of magnitude >= 64 (no unitary link has them) or non-finite
+// entries set `bad`, which makes theta non-finite.
+__device__ __forceinline__ long long q56(double x, bool &bad) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int ed = (int)((b >> 52) & 0x7FF);
+  bad |= ed > 1023 + 5;
+  const unsigned long long m = (b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+  const int sh = ed - 1019;  // x * 2^56 = m * 2^(ed - 1075 + 56)
+  unsigned long long q = sh >= 0 ? m << (sh & 15) : (sh > -64 ? m >> (-sh) : 0ull);
+  if (ed == 0) q = 0ull;  // zero and subnormals
+  const long long r = (long long)q;
+  return (long long)b < 0 ? -r : r;
+}
+template <bool NEG> __device__ __forceinline__ void accumulate_link_q(const m3<double> &u, long long acc[9], bool &bad) {
+  long long t[9];
+  t[0] = q56(u.e[1].r, bad) - q56(u.e[3].r, bad);
+  t[1] = q56(u.e[1].i, bad) + q56(u.e[3].i, bad);
+  t[2] = q56(u.e[2].r, bad) - q56(u.e[6].r, bad);
+  t[3] = q56(u.e[2].i, bad) + q56(u.e[6].i, bad);
+  t[4] = q56(u.e[5].r, bad) - q56(u.e[7].r, bad);
+  t[5] = q56(u.e[5].i, bad) + q56(u.e[7].i, bad);
+  t[6] = q56(u.e[0].i, bad);
+  t[7] = q56(u.e[4].i, bad);
+  t[8] = q56(u.e[8].i, bad);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) acc[k] = NEG ? acc[k] - t[k] : acc[k] + t[k];
+}
+
 // PT is the type of the packed output (T, or float when a double stage feeds a float FFT).
 template <typename T, int NT, typename PT = T>
 __global__ void __launch_bounds__(NT) k_delta(const T *__restrict__ U, PT *__restrict__ P, double *partials, Ctrl *ctrl,
@@ -207,6 +239,50 @@ __global__ void __launch_bounds__(NT) k_delta(const T *__restrict__ U, PT *__res
   if (!should_run<T>(ctrl, check_active)) return;
   count_run(ctrl, tkid);
   double th = 0.0, f = 0.0;
+  if constexpr (std::is_same<T, double>::value) {
+#pragma unroll 1
+    for (int k = 0; k < kSitesPerThread; ++k) {
+      const int64_t s = ((int64_t)blockIdx.x * kSitesPerThread + k) * NT + threadIdx.x;
+      if (s >= V) break;
+      int c[4];
+      site_coords(L, s, c);
+      long long acc[9];
+#pragma unroll
+      for (int e = 0; e < 9; ++e) acc[e] = 0;
+      bool bad = false;
+      double fs = 0;
+#pragma unroll
+      for (int mu = 0; mu < 4; ++mu) {
+        const double *plane = U + (int64_t)mu * link_plane_stride<T>(V);
+        m3<double> u;
+        load_link(plane, V, site_back(L, s, mu, c[mu]), u);  // U_mu(x - mu)
+        accumulate_link_q<false>(u, acc, bad);
+        load_link(plane, V, s, u);  // - U_mu(x)
+        accumulate_link_q<true>(u, acc, bad);
+        fs += u.e[0].r + u.e[4].r + u.e[8].r;  // Re Tr U_mu(x)
+      }
+      constexpr double sc = 0x1p-56;
+      double d[6];
+#pragma unroll
+      for (int e = 0; e < 6; ++e) d[e] = __ll2double_rn(acc[e]) * sc;
+      // Delta_ii = 2i (Im B_ii - mean) = 2i (3 Im B_ii - sum) / 3
+      const long long sd = acc[6] + acc[7] + acc[8];
+      constexpr double w = 2.0 / 3.0 * sc;
+      const double a0 = __ll2double_rn(3 * acc[6] - sd) * w, a1 = __ll2double_rn(3 * acc[7] - sd) * w;
+      const double a2 = __ll2double_rn(3 * acc[8] - sd) * w;
+      double ts = a0 * a0 + a1 * a1 + a2 * a2 +
+                  2 * (d[0] * d[0] + d[1] * d[1] + d[2] * d[2] + d[3] * d[3] + d[4] * d[4] + d[5] * d[5]);
+      if (bad) ts = __longlong_as_double(0x7FF8000000000000ll);  // non-finite or out-of-range link entries
+      th += ts;
+      f += fs;
+      st(P, s, mkc(convert<PT>(d[0]), convert<PT>(d[1])));
+      st(P, V + s, mkc(convert<PT>(d[2]), convert<PT>(d[3])));
+      st(P, 2 * V + s, mkc(convert<PT>(d[4]), convert<PT>(d[5])));
+      st(P, 3 * V + s, mkc(convert<PT>(a0), convert<PT>(a1)));
+    }
+    reduce_and_finalize<NT>(th, f, partials, ctrl, V, counts_update);
+    return;
+  }
 #pragma unroll 1
   for (int k = 0; k < kSitesPerThread; ++k) {
     const int64_t s = ((int64_t)blockIdx.x * kSitesPerThread + k) * NT + threadIdx.x;
@@ -249,9 +325,10 @@ __device__ __forceinline__ void unpack_scaled(const PT *P, int64_t V, int64_t s,
   const cx<PT> q0 = ldg(P, s), q1 = ldg(P, V + s), q2 = ldg(P, 2 * V + s), q3 = ldg(P, 3 * V + s);
   const cx<T> p0 = {convert<T>(q0.r), convert<T>(q0.i)}, p1 = {convert<T>(q1.r), convert<T>(q1.i)};
   const cx<T> p2 = {convert<T>(q2.r), convert<T>(q2.i)}, p3 = {convert<T>(q3.r), convert<T>(q3.i)};
-  m.e[0] = {0, a * p3.r};
-  m.e[4] = {0, a * p3.i};
-  m.e[8] = {0, -a * (p3.r + p3.i)};
+  const T zero = kconst<T>(0.0);
+  m.e[0] = {zero, a * p3.r};
+  m.e[4] = {zero, a * p3.i};
+  m.e[8] = {zero, -a * (p3.r + p3.i)};
   m.e[1] = scale(p0, a);
   m.e[2] = scale(p1, a);
   m.e[5] = scale(p2, a);
@@ -264,9 +341,50 @@ __device__ __forceinline__ void unpack_scaled(const PT *P, int64_t V, int64_t s,
 // a6: g(x) = SU(3)-projection of [1 + (alpha/2) Delta-tilde(x)] (Eq. 2 expanded to first order in
 // alpha, then reunitarized).
 // ---------------------------------------------------------------------------------------------
+//
+// Small-step form of the projection (double path): with X = (alpha/2) Delta-tilde small, Gram-Schmidt of
+// 1 + X is written as g = 1 + a, and a is formed from small quantities only, in double-float:
+//   row 0: |e0 + x0|^2 = 1 + t0, t0 = 2 Re x0_0 + |x0|^2; a0 = x0 (1 + c0) + c0 e0 with
+//          c0 = (1 + t0)^(-1/2) - 1;
+//   row 1: p = <g0, e1 + x1> = conj(a0_1) + x1_0 + sum_j conj(a0_j) x1_j; d1 = x1 - p (e0 + a0);
+//          |e1 + d1|^2 = 1 + t1, t1 = 2 Re d1_1 + |d1|^2; a1 = d1 (1 + c1) + c1 e1;
+//   row 2: conj(g0 x g1) - e2 = conj(e0 x a1 + a0 x e1 + a0 x a1).
+// (1 + t)^(-1/2) - 1 is the series -t/2 + 3t^2/8 - 5t^3/16, whose remainder is below 2^-54 for
+// |t| <= 2^-13. When every element of X is below 2^-8 in magnitude, a has an absolute error of a few
+// 2^-48 |a|, below the FP64 rounding of g, and g = 1 + a is assembled in FP64.
+constexpr int kSmallXFloatExpField = 127 - 9;  // |x| < 2^-8  <=>  float exponent field <= 118
+
+__device__ __forceinline__ int fexp_field(float x) { return (int)((__float_as_uint(x) >> 23) & 0xFF); }
+__device__ __forceinline__ df64 rsqrt1p_m1(df64 t) {
+  return t * (kconst<df64>(-0.5) + t * (kconst<df64>(0.375) + t * kconst<df64>(-0.3125)));
+}
+__device__ __forceinline__ void small_step_projection(const m3<df64> &X, m3<df64> &a) {
+  const df64 one = kconst<df64>(1.0);
+  const df64 t0 = kconst<df64>(2.0) * X.e[0].r + (norm2(X.e[0]) + norm2(X.e[1]) + norm2(X.e[2]));
+  const df64 c0 = rsqrt1p_m1(t0), s0 = one + c0;
+  a.e[0] = scale(X.e[0], s0) + cx<df64>{c0, kconst<df64>(0.0)};
+  a.e[1] = scale(X.e[1], s0);
+  a.e[2] = scale(X.e[2], s0);
+  cx<df64> p = conjg(a.e[1]) + X.e[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) p = p + conjg(a.e[j]) * X.e[3 + j];
+  cx<df64> d[3];
+  d[0] = X.e[3] - p - p * a.e[0];
+  d[1] = X.e[4] - p * a.e[1];
+  d[2] = X.e[5] - p * a.e[2];
+  const df64 t1 = kconst<df64>(2.0) * d[1].r + (norm2(d[0]) + norm2(d[1]) + norm2(d[2]));
+  const df64 c1 = rsqrt1p_m1(t1), s1 = one + c1;
+  a.e[3] = scale(d[0], s1);
+  a.e[4] = scale(d[1], s1) + cx<df64>{c1, kconst<df64>(0.0)};
+  a.e[5] = scale(d[2], s1);
+  a.e[6] = conjg(a.e[1] * a.e[5] - a.e[2] * a.e[4] - a.e[2]);
+  a.e[7] = conjg(a.e[2] * a.e[3] - a.e[0] * a.e[5] - a.e[5]);
+  a.e[8] = conjg(a.e[0] * a.e[4] - a.e[1] * a.e[3] + a.e[4] + a.e[0]);
+}
+
 template <typename T, int NT, typename PT = T>
 __global__ void __launch_bounds__(NT) k_gauge(const PT *__restrict__ P, T *__restrict__ G, T half_alpha, int64_t V,
-                                             const Ctrl *ctrl, int check_active, int tkid) {
+                                             const Ctrl *ctrl, int check_active, int tkid, int allow_small) {
   {
     const int cfg = blockIdx.z;
     P += (int64_t)cfg * 4 * V * 2;
@@ -277,6 +395,24 @@ __global__ void __launch_bounds__(NT) k_gauge(const PT *__restrict__ P, T *__res
   count_run(ctrl, tkid);
   const int64_t s = (int64_t)blockIdx.x * NT + threadIdx.x;
   if (s >= V) return;
+  if constexpr (std::is_same<T, double>::value) {
+    m3<df64> X;
+    unpack_scaled<df64, PT>(P, V, s, convert<df64>(half_alpha), X);
+    int ef = 0;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) ef = max(ef, max(fexp_field(X.e[e].r.hi), fexp_field(X.e[e].i.hi)));
+    if (__all_sync(__activemask(), allow_small && ef <= kSmallXFloatExpField)) {
+      m3<df64> a;
+      small_step_projection(X, a);
+#pragma unroll
+      for (int e = 0; e < 9; ++e) {
+        double re = convert<double>(a.e[e].r);
+        if (e == 0 || e == 4 || e == 8) re = 1.0 + re;
+        st(G, (int64_t)e * V + s, mkc(re, convert<double>(a.e[e].i)));
+      }
+      return;
+    }
+  }
   m3<T> g;
   unpack_scaled<T, PT>(P, V, s, half_alpha, g);
   g.e[0].r += 1;
@@ -289,10 +425,144 @@ __global__ void __launch_bounds__(NT) k_gauge(const PT *__restrict__ P, T *__res
 
 // ---------------------------------------------------------------------------------------------
 // a7: U_mu(x) -> g(x) U_mu(x) g^dagger(x + mu) for the four directions.
+//
+// Double links take one of two forms of the same product, chosen per warp and per link:
+//  * small step: with g(x) = 1 + a and g(x+mu) = 1 + b, the new link is U + delta with
+//      delta = a U + (U + a U) b^dagger,
+//    delta formed in double-float arithmetic (FP32 operations, ~2^-48 relative) and added to U in
+//    FP64. When every element of a and b is below 2^-7 in magnitude, delta's absolute error (a few
+//    2^-48 |a| |U|) is at or below the FP64 rounding of the product itself, and the FP64 pipe -- 1/64
+//    of the FP32 rate on this GPU -- does only the final additions. Near convergence |a| ~ alpha |Delta|
+//    is far below the bound.
+//  * general step: rows 0 and 1 of g(x) U g^+(x+mu) by FP64 products, row 2 = conj(row0 x row1).
 // ---------------------------------------------------------------------------------------------
+constexpr int kSmallStepExpField = 1023 - 8;  // |x| < 2^-7  <=>  biased FP64 exponent <= 1015
+
+__device__ __forceinline__ int exp_field(double x) {
+  return (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FF);
+}
+// Element e of g - 1 in double-float, and the largest exponent field of its parts so far.
+__device__ __forceinline__ cx<df64> minus_identity_df(cx<double> v, int e, int &emax) {
+  if (e == 0 || e == 4 || e == 8) v.r -= 1.0;  // exact for |g_ii - 1| <= 1/2 (Sterbenz)
+  emax = max(emax, max(exp_field(v.r), exp_field(v.i)));
+  return {df64_split_fast(v.r), df64_split_fast(v.i)};
+}
+__device__ __forceinline__ cx<df64> dfc_add(cx<df64> x, cx<df64> y) { return {x.r + y.r, x.i + y.i}; }
+__device__ __forceinline__ double df64_widen(df64 x) { return widen_bits(x.hi) + widen_bits(x.lo); }
+
+// Asynchronous 16-byte global -> shared copies (each thread copies, and later reads, only its own slots,
+// so completing its own groups is all the ordering needed).
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Shared memory of the double update per block of NT threads, [slot][thread] in 16-byte units:
+// a = g(x) - 1 in double-float (9 slots), two buffers of links (2 x 9), g(x+mu) (9).
+template <int NT> constexpr size_t update_smem_bytes() { return (size_t)36 * NT * 16; }
+
+// Start the copies of link mu at site s (9 elements to bu) and of g at its forward neighbour sf (to bg).
+template <int NT>
+__device__ __forceinline__ void fetch_link(const double *plane, const double *G, int64_t V, int64_t s, int64_t sf,
+                                           double2 *bu, double2 *bg) {
+  const double2 *pu = reinterpret_cast<const double2 *>(plane);
+  const double2 *pg = reinterpret_cast<const double2 *>(G);
+#pragma unroll
+  for (int e = 0; e < 9; ++e) {
+    cp_async16(bu + e * NT + threadIdx.x, pu + (int64_t)e * V + s);
+    cp_async16(bg + e * NT + threadIdx.x, pg + (int64_t)e * V + sf);
+  }
+  cp_async_commit();
+}
+
+// Small-step update of one link: u (the link) and b = g(x+mu) - 1 in double-float registers, a (rows of
+// g(x) - 1) in shared memory, the FP64 link in bu; the new link is stored to the plane.
+template <int NT>
+__device__ __forceinline__ void update_link_small(double *plane, int64_t V, int64_t s, const float4 *sa,
+                                                  const double2 *bu, const cx<df64> u[9], const cx<df64> b[9]) {
+  // rows one at a time (a rolled loop keeps the code within the instruction cache)
+#pragma unroll 1
+  for (int i = 0; i < 3; ++i) {
+    cx<df64> ai[3], ui[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      ai[k] = from_vec<df64>(sa[(3 * i + k) * NT + threadIdx.x]);
+      ui[k] = i == 0 ? u[k] : (i == 1 ? u[3 + k] : u[6 + k]);
+    }
+    cx<df64> v[3], y[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {  // v = row i of a U
+      dfacc re = {0.f, 0.f}, im = {0.f, 0.f};
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        dfacc_mac(re, ai[k].r, u[3 * k + j].r);
+        dfacc_msub(re, ai[k].i, u[3 * k + j].i);
+        dfacc_mac(im, ai[k].r, u[3 * k + j].i);
+        dfacc_mac(im, ai[k].i, u[3 * k + j].r);
+      }
+      v[j] = {dfacc_result(re), dfacc_result(im)};
+      y[j] = dfc_add(ui[j], v[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {  // delta_ij = v_j + sum_k y_k conj(b_jk); new U_ij = U_ij + delta_ij
+      dfacc re = dfacc_from(v[j].r), im = dfacc_from(v[j].i);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        dfacc_mac(re, y[k].r, b[3 * j + k].r);
+        dfacc_mac(re, y[k].i, b[3 * j + k].i);
+        dfacc_mac(im, y[k].i, b[3 * j + k].r);
+        dfacc_msub(im, y[k].r, b[3 * j + k].i);
+      }
+      const int e = 3 * i + j;
+      const double2 old = bu[e * NT + threadIdx.x];
+      st(plane, (int64_t)e * V + s, mkc(old.x + df64_widen(dfacc_result(re)), old.y + df64_widen(dfacc_result(im))));
+    }
+  }
+}
+
+// General-step update of one link in FP64: rows 0 and 1 of g(x) U g^+(x+mu) by products (g(x) from
+// global memory, the link from bu, g(x+mu) from bg), row 2 = conj(row0 x row1).
+template <int NT>
+__device__ __forceinline__ void update_link_general(double *plane, const double *G, int64_t V, int64_t s,
+                                                    const double2 *bu, const double2 *bg) {
+  m3<double> t;
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    cx<double> gi[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) gi[k] = ldg(G, (int64_t)(3 * i + k) * V + s);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      cx<double> acc = gi[0] * from_vec<double>(bu[j * NT + threadIdx.x]);
+      acc = cmac(acc, gi[1], from_vec<double>(bu[(3 + j) * NT + threadIdx.x]));
+      acc = cmac(acc, gi[2], from_vec<double>(bu[(6 + j) * NT + threadIdx.x]));
+      t.e[3 * i + j] = acc;
+    }
+  }
+  m3<double> o;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const cx<double> h0 = from_vec<double>(bg[(3 * j) * NT + threadIdx.x]);
+    const cx<double> h1 = from_vec<double>(bg[(3 * j + 1) * NT + threadIdx.x]);
+    const cx<double> h2 = from_vec<double>(bg[(3 * j + 2) * NT + threadIdx.x]);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      cx<double> acc = {0, 0};
+      acc = cmac_cj(acc, t.e[3 * i], h0);
+      acc = cmac_cj(acc, t.e[3 * i + 1], h1);
+      acc = cmac_cj(acc, t.e[3 * i + 2], h2);
+      o.e[3 * i + j] = acc;
+    }
+  }
+  store_link(plane, V, s, o);
+}
+
 template <typename T, int NT>
-__global__ void __launch_bounds__(NT) k_update(T *__restrict__ U, const T *__restrict__ G, Lattice L, const Ctrl *ctrl,
-                                              int check_active, int tkid) {
+__global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 3 : 2)
+    k_update(T *__restrict__ U, const T *__restrict__ G, Lattice L, const Ctrl *ctrl, int check_active, int tkid,
+             int allow_small) {
   const int64_t V = L.V;
   {
     const int cfg = blockIdx.z;
@@ -306,21 +576,63 @@ __global__ void __launch_bounds__(NT) k_update(T *__restrict__ U, const T *__res
   if (s >= V) return;
   int c[4];
   site_coords(L, s, c);
-  m3<T> gx;
+  if constexpr (std::is_same<T, double>::value) {
+    // The copies of link mu + 1 run while link mu is computed (dynamic shared memory of
+    // update_smem_bytes<NT>()).
+    extern __shared__ __align__(16) unsigned char update_smem[];
+    float4 *sa = reinterpret_cast<float4 *>(update_smem);
+    double2 *bu0 = reinterpret_cast<double2 *>(sa + 9 * NT);
+    double2 *bg = bu0 + 18 * NT;
+    const int64_t pstride = link_plane_stride<T>(V);
+    fetch_link<NT>(U, G, V, s, site_fwd(L, s, 0, c[0]), bu0, bg);
+    int ea = 0;
 #pragma unroll
-  for (int e = 0; e < 9; ++e) gx.e[e] = ldg(G, (int64_t)e * V + s);
+    for (int e = 0; e < 9; ++e)
+      sa[e * NT + threadIdx.x] = to_vec<df64>(minus_identity_df(ldg(G, (int64_t)e * V + s), e, ea));
 #pragma unroll 1
-  for (int mu = 0; mu < 4; ++mu) {
-    const int64_t sf = site_fwd(L, s, mu, c[mu]);
-    T *plane = U + (int64_t)mu * link_plane_stride<T>(V);
-    m3<T> u, gy, t;
-    load_link(plane, V, s, u);
+    for (int mu = 0; mu < 4; ++mu) {
+      double *plane = U + (int64_t)mu * pstride;
+      const double2 *bu = bu0 + (mu & 1) * 9 * NT;
+      cp_async_wait_all();
+      cx<df64> b[9];
+      int eb = ea;
 #pragma unroll
-    for (int e = 0; e < 9; ++e) gy.e[e] = ldg(G, (int64_t)e * V + sf);
-    // rows 0 and 1 of g(x) U g^+(x+mu) by products, row 2 = conj(row0 x row1) (the result is in SU(3))
-    mul_rows01(gx, u, t);
-    mul_adj_rows01(t, gy, u);
-    store_link(plane, V, s, u);
+      for (int e = 0; e < 9; ++e) b[e] = minus_identity_df(from_vec<double>(bg[e * NT + threadIdx.x]), e, eb);
+      if (__all_sync(__activemask(), allow_small && eb <= kSmallStepExpField)) {
+        cx<df64> u[9];
+#pragma unroll
+        for (int e = 0; e < 9; ++e) {
+          const double2 v = bu[e * NT + threadIdx.x];
+          u[e] = {df64_split_fast(v.x), df64_split_fast(v.y)};
+        }
+        if (mu < 3)
+          fetch_link<NT>(plane + pstride, G, V, s, site_fwd(L, s, mu + 1, c[mu + 1]), bu0 + ((mu + 1) & 1) * 9 * NT,
+                         bg);
+        update_link_small<NT>(plane, V, s, sa, bu, u, b);
+      } else {
+        update_link_general<NT>(plane, G, V, s, bu, bg);
+        if (mu < 3)
+          fetch_link<NT>(plane + pstride, G, V, s, site_fwd(L, s, mu + 1, c[mu + 1]), bu0 + ((mu + 1) & 1) * 9 * NT,
+                         bg);
+      }
+    }
+  } else {
+    m3<T> gx;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) gx.e[e] = ldg(G, (int64_t)e * V + s);
+#pragma unroll 1
+    for (int mu = 0; mu < 4; ++mu) {
+      const int64_t sf = site_fwd(L, s, mu, c[mu]);
+      T *plane = U + (int64_t)mu * link_plane_stride<T>(V);
+      m3<T> u, gy, t;
+      load_link(plane, V, s, u);
+#pragma unroll
+      for (int e = 0; e < 9; ++e) gy.e[e] = ldg(G, (int64_t)e * V + sf);
+      // rows 0 and 1 of g(x) U g^+(x+mu) by products, row 2 = conj(row0 x row1) (the result is in SU(3))
+      mul_rows01(gx, u, t);
+      mul_adj_rows01(t, gy, u);
+      store_link(plane, V, s, u);
+    }
   }
 }
 
