@@ -40,6 +40,10 @@ UNIT = "site-iterations/s"
 # x 2.07 GHz = 1.259 TFLOP/s (GB300 FP64 is 1.25 TFLOP/s nominal).
 FP64_FLOP_PER_CLK = 152 * 2 * 2      # 152 SMs x 2 DFMA per clock x 2 flop
 FP32_OPS_PER_CLK = 152 * 128         # 152 SMs x 128 FP32 lanes (one FADD, FMUL or FFMA each per clock)
+# DRAM bytes (read + write) per launch of a kernel at 64^4, from one ncu capture of
+# dram__bytes_read.sum + dram__bytes_write.sum (profiles/gauge_update_f64_64x4_traffic.md); valid only
+# for the kernel version that was captured.
+TRAFFIC_64 = {"gauge_update.f64": 14.53e9 + 9.89e9}
 
 
 def peaks():
@@ -171,9 +175,10 @@ def run_reference(args, dims, rank, ws):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config_of(args, dims, "fp64 CPU oracle"),
+            "data": "synthetic", "config": config_of(args, dims, args.precision),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": "%d iterations of Algorithm 1 on the %s configuration" % (args.steps, "x".join(map(str, dims)))},
+                             "sample": "%d iterations of Algorithm 1 (FP64 CPU oracle) on the %s configuration"
+                                       % (args.steps, "x".join(map(str, dims)))},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -478,7 +483,8 @@ def main():
     if kind and dk["alu_frac"] > dk["hbm_frac"]:
         pk, unit, src = alu_peak[kind]
         roof = {"bound": "alu", "achieved": round(f / per / 1e12, 4), "peak": round(pk / 1e12, 4),
-                "unit": unit, "frac": round(f / per / pk, 4), "traffic": None,
+                "unit": unit, "frac": round(f / per / pk, 4),
+                "traffic": TRAFFIC_64.get(dom) if tuple(dims) == (64, 64, 64, 64) else None,
                 "kernel": dom, "peak_source": "derived: %s x median SM clock under load" % src}
     else:
         roof = {"bound": "hbm", "achieved": round(b / per / 1e9, 1), "peak": hbm, "unit": "GB/s",

@@ -44,7 +44,8 @@ typedef enum {
 } lgf_status;
 
 typedef enum {
-  LGF_FP64 = 0,  /* every step in double precision                                               */
+  LGF_FP64 = 0,  /* every step at double precision: FP64 links and sums (equivalent forms of some
+                    steps are listed at lgf_create)                                              */
   LGF_MIXED = 1, /* float links, FFTs and updates (double reductions) until theta <= theta_switch,
                     then a double-precision handover and double precision to theta < eps         */
   LGF_FP32 = 2   /* float links, FFTs and updates throughout (double reductions)                 */
@@ -74,9 +75,10 @@ void lgf_default_options(lgf_options *opt);
  * tests): LGF_GENERIC_FFT=1 uses the generic FFT passes for every extent; LGF_FFT_NATIVE_F64=1 runs
  * the Fourier filter of the double path in IEEE double instead of double-float; and LGF_SMALL_STEP=0
  * turns off the small-step forms of the double path, which by default apply per warp where the step
- * is small: g = 1 + a formed in double-float when every |(alpha/2) Delta-tilde| < 2^-8, and the update
- * U + [a U + (U + a U) b^+] (a = g(x) - 1, b = g(x+mu) - 1) with the bracket in double-float when
- * every |a|, |b| < 2^-7. Their errors are at the level of the FP64 rounding of the plain forms. */
+ * is small: g = 1 + a formed in double-float when every |(alpha/2) Delta-tilde| < 2^-8, and rows 0-1
+ * of the update as U + [a U + (U + a U) b^+] (a = g(x) - 1, b = g(x+mu) - 1) with the bracket in
+ * double-float when every |a|, |b| < 2^-7 (row 2 = conj(row0 x row1) in FP64 in both forms). Their
+ * errors are at the level of the FP64 rounding of the plain forms. */
 lgf_status lgf_create(int Nx, int Ny, int Nz, int Nt, lgf_ctx **out);
 
 /* Release every resource of the context (NULL is accepted). */

@@ -1,9 +1,12 @@
 // df64.cuh -- double-float ("df64") numbers: an unevaluated sum hi + lo of two floats (|lo| <= ulp(hi)/2),
 // a 48-bit significand built from FP32 operations. On this GPU the FP64 pipe runs at 1/64 of the FP32
-// rate, so the Fourier filter of the double-precision path runs in df64: its error (~2^-47 relative to
-// the norm of the field) is far below what the 1e-12 agreement with the FP64 oracle needs, and the
-// filter only sets the direction of the gauge update; links, Delta, g, the update and the theta/F sums
-// stay in IEEE double.
+// rate, so the double-precision path does in df64 what does not need IEEE double:
+//  * the Fourier filter: its error (~2^-47 relative to the norm of the field) is far below the 1e-12
+//    agreement with the FP64 oracle, and the filter only sets the direction of the gauge update;
+//  * the small-step forms of g and of the gauge update, which compute only the deviation of g from 1
+//    (and the change of the link) in df64: that deviation is small, so its df64 error is at or below
+//    the FP64 rounding of the result, which is assembled in FP64.
+// Links, the theta/F sums and the general (large-step) forms stay in IEEE double.
 //
 // Building blocks (error-free transformations): TwoSum (Knuth), FastTwoSum (Dekker, |a| >= |b|) and
 // TwoProd with a fused multiply-add; the double-word operations follow Joldes, Muller, Popescu,
@@ -149,6 +152,14 @@ struct dfacc {
   float s, c;
 };
 __device__ __forceinline__ dfacc dfacc_from(df64 x) { return {x.hi, x.lo}; }
+// an accumulator holding the exact product x*y (to the dropped lo*lo term)
+__device__ __forceinline__ dfacc dfacc_prod(df64 x, df64 y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  return {p, e};
+}
 __device__ __forceinline__ void dfacc_mac(dfacc &a, df64 x, df64 y) {
   const float p = __fmul_rn(x.hi, y.hi);
   float e = __fmaf_rn(x.hi, y.hi, -p);

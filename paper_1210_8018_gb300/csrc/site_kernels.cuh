@@ -427,10 +427,10 @@ __global__ void __launch_bounds__(NT) k_gauge(const PT *__restrict__ P, T *__res
 // a7: U_mu(x) -> g(x) U_mu(x) g^dagger(x + mu) for the four directions.
 //
 // Double links take one of two forms of the same product, chosen per warp and per link:
-//  * small step: with g(x) = 1 + a and g(x+mu) = 1 + b, the new link is U + delta with
+//  * small step: with g(x) = 1 + a and g(x+mu) = 1 + b, rows 0 and 1 of the new link are U + delta with
 //      delta = a U + (U + a U) b^dagger,
 //    delta formed in double-float arithmetic (FP32 operations, ~2^-48 relative) and added to U in
-//    FP64. When every element of a and b is below 2^-7 in magnitude, delta's absolute error (a few
+//    FP64; row 2 = conj(row0 x row1) in FP64. When every element of a and b is below 2^-7 in magnitude, delta's absolute error (a few
 //    2^-48 |a| |U|) is at or below the FP64 rounding of the product itself, and the FP64 pipe -- 1/64
 //    of the FP32 rate on this GPU -- does only the final additions. Near convergence |a| ~ alpha |Delta|
 //    is far below the bound.
@@ -448,6 +448,7 @@ __device__ __forceinline__ cx<df64> minus_identity_df(cx<double> v, int e, int &
   return {df64_split_fast(v.r), df64_split_fast(v.i)};
 }
 __device__ __forceinline__ cx<df64> dfc_add(cx<df64> x, cx<df64> y) { return {x.r + y.r, x.i + y.i}; }
+// (integer widening: the float -> double conversion instruction occupies the FP64 pipe)
 __device__ __forceinline__ double df64_widen(df64 x) { return widen_bits(x.hi) + widen_bits(x.lo); }
 
 // Asynchronous 16-byte global -> shared copies (each thread copies, and later reads, only its own slots,
@@ -481,22 +482,25 @@ __device__ __forceinline__ void fetch_link(const double *plane, const double *G,
 // g(x) - 1) in shared memory, the FP64 link in bu; the new link is stored to the plane.
 template <int NT>
 __device__ __forceinline__ void update_link_small(double *plane, int64_t V, int64_t s, const float4 *sa,
-                                                  const double2 *bu, const cx<df64> u[9], const cx<df64> b[9]) {
-  // rows one at a time (a rolled loop keeps the code within the instruction cache)
+                                                  double2 *bu, const cx<df64> u[9], const cx<df64> b[9]) {
+  // rows 0 and 1 one at a time (a rolled loop keeps the code within the instruction cache); each new
+  // element replaces the old one in bu
 #pragma unroll 1
-  for (int i = 0; i < 3; ++i) {
+  for (int i = 0; i < 2; ++i) {
     cx<df64> ai[3], ui[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       ai[k] = from_vec<df64>(sa[(3 * i + k) * NT + threadIdx.x]);
-      ui[k] = i == 0 ? u[k] : (i == 1 ? u[3 + k] : u[6 + k]);
+      ui[k] = i == 0 ? u[k] : u[3 + k];
     }
     cx<df64> v[3], y[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {  // v = row i of a U
-      dfacc re = {0.f, 0.f}, im = {0.f, 0.f};
+      dfacc re = dfacc_prod(ai[0].r, u[j].r), im = dfacc_prod(ai[0].r, u[j].i);
+      dfacc_msub(re, ai[0].i, u[j].i);
+      dfacc_mac(im, ai[0].i, u[j].r);
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
+      for (int k = 1; k < 3; ++k) {
         dfacc_mac(re, ai[k].r, u[3 * k + j].r);
         dfacc_msub(re, ai[k].i, u[3 * k + j].i);
         dfacc_mac(im, ai[k].r, u[3 * k + j].i);
@@ -517,9 +521,21 @@ __device__ __forceinline__ void update_link_small(double *plane, int64_t V, int6
       }
       const int e = 3 * i + j;
       const double2 old = bu[e * NT + threadIdx.x];
-      st(plane, (int64_t)e * V + s, mkc(old.x + df64_widen(dfacc_result(re)), old.y + df64_widen(dfacc_result(im))));
+      const double2 nu = make_double2(old.x + df64_widen(dfacc_result(re)), old.y + df64_widen(dfacc_result(im)));
+      bu[e * NT + threadIdx.x] = nu;
+      st(plane, (int64_t)e * V + s, from_vec<double>(nu));
     }
   }
+  // row 2 = conj(row0 x row1) in FP64, as in the general form (the FP64 pipe has room here)
+  cx<double> r0[3], r1[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    r0[j] = from_vec<double>(bu[j * NT + threadIdx.x]);
+    r1[j] = from_vec<double>(bu[(3 + j) * NT + threadIdx.x]);
+  }
+  st(plane, 6 * V + s, cross_cj(r0[1], r1[2], r0[2], r1[1]));
+  st(plane, 7 * V + s, cross_cj(r0[2], r1[0], r0[0], r1[2]));
+  st(plane, 8 * V + s, cross_cj(r0[0], r1[1], r0[1], r1[0]));
 }
 
 // General-step update of one link in FP64: rows 0 and 1 of g(x) U g^+(x+mu) by products (g(x) from
@@ -608,7 +624,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 3 : 2)
         if (mu < 3)
           fetch_link<NT>(plane + pstride, G, V, s, site_fwd(L, s, mu + 1, c[mu + 1]), bu0 + ((mu + 1) & 1) * 9 * NT,
                          bg);
-        update_link_small<NT>(plane, V, s, sa, bu, u, b);
+        update_link_small<NT>(plane, V, s, sa, bu0 + (mu & 1) * 9 * NT, u, b);
       } else {
         update_link_general<NT>(plane, G, V, s, bu, bg);
         if (mu < 3)
