@@ -79,17 +79,18 @@ def algorithmic(kernel, dims):
         # packed Delta-tilde read, g written
         "gauge_g": ((4 + 9) * es, 160),
         # links read and written, g read (neighbours are the same data). Double: the small-step form,
-        # which every warp of the double stage takes: per link two 3x3 complex products in double-float,
-        # 9 x 3 x 4 x 2 = 216 real multiply-accumulates of 12 FP32 operations each (Dot2 step). Float
-        # (plain FP32 schedule): rows 0-1 of g U and of (g U) g^+, row 2 by a cross product, 336 flop.
-        "gauge_update": ((4 * lp * 2 + 9) * es, 4 * 216 * 12 if prec == "f64" else 4 * 336),
+        # which every warp of the double stage takes: per link, rows 0-1 of two 3x3 complex products in
+        # double-float, 6 outputs x 3 terms x 4 real products x 2 = 144 multiply-accumulates of 12 FP32
+        # operations each (Dot2 step); row 2 by an FP64 cross product (not counted). Float (plain FP32
+        # schedule): rows 0-1 of g U and of (g U) g^+, row 2 by a cross product, 336 flop.
+        "gauge_update": ((4 * lp * 2 + 9) * es, 4 * 144 * 12 if prec == "f64" else 4 * 336),
         # float stage: links read and written, G read and written (rows 0-1), packed Delta-tilde read (g is
         # rebuilt in registers); the _reunit variant also projects the new links in double precision
         "gauge_update_fused": ((4 * lp * 2 + 12 + 4) * es, 0),
         "gauge_update_fused_reunit": ((4 * lp * 2 + 12 + 4) * es, 4 * 170),
         "gacc_to_double": (6 * 8 + 9 * 16, 170),
         "handover_transform": (36 * 16 * 2 + 9 * 16, 4 * 336),
-        "to_planes": (36 * 16 + 4 * lp * es, 0),
+        "to_planes": (4 * lp * 16 + 4 * lp * es, 0),  # the float load reads rows 0-1 of each link only
         "from_planes": (4 * lp * es + 36 * 16, 0),
         "set_identity": (6 * 8, 0),
     }
@@ -517,6 +518,7 @@ def main():
                 "dtype": {"mixed": "f32+f64", "fp64": "f64", "fp32": "f32"}[args.precision],
                 "data": "synthetic", "config": config_of(args, dims, args.precision),
                 "iters_per_step": iters[0], "time_to_theta_s": {args.precision: t_max / args.steps / 1e3},
+                "theta": r["theta"], "F": r["F"],
                 "roofline": roof, "gpu_launches": gpu_launches, "clocks": clocks, "e2e": e2e,
                 "kernels": kernels}
         if fp64:
