@@ -489,7 +489,8 @@ def main():
                 "kernel": dom, "peak_source": "derived: %s x median SM clock under load" % src}
     else:
         roof = {"bound": "hbm", "achieved": round(b / per / 1e9, 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(b / per / 1e9 / hbm, 4), "traffic": None, "kernel": dom,
+                "frac": round(b / per / 1e9 / hbm, 4),
+                "traffic": TRAFFIC_64.get(dom) if tuple(dims) == (64, 64, 64, 64) else None, "kernel": dom,
                 "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % which}
 
     # end to end through the C ABI from pinned host buffers (H2D + fix + D2H inside the timed region)

@@ -1,4 +1,5 @@
-"""Compile the CUDA library liblgf.so in-tree for sm_103a (nvcc, one translation unit)."""
+"""Compile the CUDA library liblgf.so in-tree for sm_103a: nvcc compiles the translation units in
+parallel (the host code and per-type FFT units), then links them."""
 import os
 import subprocess
 

@@ -108,6 +108,23 @@ __device__ __forceinline__ double widen_bits(float f) {
                                   ((unsigned long long)(u & 0x7FFFFFu) << 29);  // Inf/NaN map to Inf/NaN
   return __longlong_as_double((long long)bits);
 }
+// double -> float, rounded to nearest (ties to even), with integer operations only. Results below the
+// smallest normal float (2^-126) give a signed zero, results beyond the float range infinity (and NaN
+// stays NaN): the fields converted here are O(1).
+__device__ __forceinline__ float narrow_bits(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned hi32 = (unsigned)(b >> 32), lo32 = (unsigned)b;
+  const unsigned sign = hi32 & 0x80000000u;
+  const int ed = (int)((hi32 >> 20) & 0x7FF);
+  const int ef = ed - 896;
+  if (ed == 0x7FF) return __uint_as_float(sign | 0x7F800000u | ((((hi32 & 0xFFFFFu) | lo32) != 0) ? 0x400000u : 0u));
+  if (ef < 1) return __uint_as_float(sign);
+  if (ef > 254) return __uint_as_float(sign | 0x7F800000u);
+  const unsigned m = ((hi32 & 0xFFFFFu) << 3) | (lo32 >> 29);  // top 23 stored mantissa bits
+  const unsigned rest = lo32 & 0x1FFFFFFFu;                      // the 29 bits rounded away
+  const unsigned up = (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;
+  return __uint_as_float(sign | ((((unsigned)ef << 23) | m) + up));  // a carry moves into the exponent
+}
 template <> struct Conv<df64, double> {
   __device__ __forceinline__ static df64 f(double s) { return df64_split_bits(s); }
 };

@@ -145,13 +145,18 @@ __device__ __forceinline__ void fft_stage(cx<T> *tile, const cx<T> *tw, int N, i
     cx<T> v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = tile[base + st * M * r];
+    // (a stage with M = 1 has j = 0 and unit twiddles: no multiplications; M is uniform per stage)
     if constexpr (!INV) {
       dft<T, R, false>(v);
+      if (M > 1) {
 #pragma unroll
-      for (int r = 1; r < R; ++r) v[r] = v[r] * tw[j * r * twstep];
+        for (int r = 1; r < R; ++r) v[r] = v[r] * tw[j * r * twstep];
+      }
     } else {
+      if (M > 1) {
 #pragma unroll
-      for (int r = 1; r < R; ++r) v[r] = v[r] * conjg(tw[j * r * twstep]);
+        for (int r = 1; r < R; ++r) v[r] = v[r] * conjg(tw[j * r * twstep]);
+      }
       dft<T, R, true>(v);
     }
 #pragma unroll

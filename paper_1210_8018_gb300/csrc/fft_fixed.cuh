@@ -41,13 +41,18 @@ __device__ __forceinline__ void fx_stage(cx<T> *tile, const cx<T> *tw, int estri
     cx<T> v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = p[r * M * estride];
+    // (the last stage, M = 1, has j = 0 and unit twiddles: no multiplications)
     if constexpr (!INV) {
       dft<T, R, false>(v);
+      if constexpr (M > 1) {
 #pragma unroll
-      for (int r = 1; r < R; ++r) v[r] = v[r] * tw[j * r * TWSTEP];
+        for (int r = 1; r < R; ++r) v[r] = v[r] * tw[j * r * TWSTEP];
+      }
     } else {
+      if constexpr (M > 1) {
 #pragma unroll
-      for (int r = 1; r < R; ++r) v[r] = v[r] * conjg(tw[j * r * TWSTEP]);
+        for (int r = 1; r < R; ++r) v[r] = v[r] * conjg(tw[j * r * TWSTEP]);
+      }
       dft<T, R, true>(v);
     }
 #pragma unroll

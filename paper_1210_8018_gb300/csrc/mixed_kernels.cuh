@@ -58,12 +58,14 @@ __global__ void __launch_bounds__(NT) k_update_fused_f32(float *__restrict__ U, 
     mul_rows01(gx, u, t);
     mul_adj_rows01(t, gy, u);
     if constexpr (REUNIT) {
+      // (float <-> double by integer operations: the conversion instructions would share the FP64 pipe
+      // with the projection)
       m3<double> d;
 #pragma unroll
-      for (int e = 0; e < 6; ++e) d.e[e] = {(double)u.e[e].r, (double)u.e[e].i};
+      for (int e = 0; e < 6; ++e) d.e[e] = {widen_bits(u.e[e].r), widen_bits(u.e[e].i)};
       reunitarize(d);
 #pragma unroll
-      for (int e = 0; e < 6; ++e) u.e[e] = {(float)d.e[e].r, (float)d.e[e].i};
+      for (int e = 0; e < 6; ++e) u.e[e] = {narrow_bits(d.e[e].r), narrow_bits(d.e[e].i)};
     }
     store_link(plane, V, s, u);
   }
@@ -80,7 +82,7 @@ __global__ void __launch_bounds__(NT) k_gacc_to_double(const float *__restrict__
 #pragma unroll
   for (int e = 0; e < 6; ++e) {
     const cx<float> v = ldg(Gacc, (int64_t)e * V + s);
-    m.e[e] = {(double)v.r, (double)v.i};
+    m.e[e] = {widen_bits(v.r), widen_bits(v.i)};
   }
   reunitarize(m);
 #pragma unroll

@@ -224,6 +224,11 @@ template <bool NEG> __device__ __forceinline__ void accumulate_link_q(const m3<d
   for (int k = 0; k < 9; ++k) acc[k] = NEG ? acc[k] - t[k] : acc[k] + t[k];
 }
 
+// A float per-site value as a double by integer operations (the conversion instruction would occupy
+// the FP64 pipe); doubles pass through.
+__device__ __forceinline__ double widen_exact(float v) { return widen_bits(v); }
+__device__ __forceinline__ double widen_exact(double v) { return v; }
+
 // PT is the type of the packed output (T, or float when a double stage feeds a float FFT).
 template <typename T, int NT, typename PT = T>
 __global__ void __launch_bounds__(NT) k_delta(const T *__restrict__ U, PT *__restrict__ P, double *partials, Ctrl *ctrl,
@@ -280,41 +285,40 @@ __global__ void __launch_bounds__(NT) k_delta(const T *__restrict__ U, PT *__res
       st(P, 2 * V + s, mkc(convert<PT>(d[4]), convert<PT>(d[5])));
       st(P, 3 * V + s, mkc(convert<PT>(a0), convert<PT>(a1)));
     }
-    reduce_and_finalize<NT>(th, f, partials, ctrl, V, counts_update);
-    return;
-  }
+  } else {
 #pragma unroll 1
-  for (int k = 0; k < kSitesPerThread; ++k) {
-    const int64_t s = ((int64_t)blockIdx.x * kSitesPerThread + k) * NT + threadIdx.x;
-    if (s >= V) break;
-    int c[4];
-    site_coords(L, s, c);
-    T acc[9];
+    for (int k = 0; k < kSitesPerThread; ++k) {
+      const int64_t s = ((int64_t)blockIdx.x * kSitesPerThread + k) * NT + threadIdx.x;
+      if (s >= V) break;
+      int c[4];
+      site_coords(L, s, c);
+      T acc[9];
 #pragma unroll
-    for (int e = 0; e < 9; ++e) acc[e] = 0;
-    T fs = 0;
+      for (int e = 0; e < 9; ++e) acc[e] = 0;
+      T fs = 0;
 #pragma unroll
-    for (int mu = 0; mu < 4; ++mu) {
-      const T *plane = U + (int64_t)mu * link_plane_stride<T>(V);
-      m3<T> u;
-      load_link(plane, V, site_back(L, s, mu, c[mu]), u);  // U_mu(x - mu)
-      accumulate_link(u, (T)1, acc);
-      load_link(plane, V, s, u);  // - U_mu(x)
-      accumulate_link(u, (T)-1, acc);
-      fs += u.e[0].r + u.e[4].r + u.e[8].r;  // Re Tr U_mu(x)
+      for (int mu = 0; mu < 4; ++mu) {
+        const T *plane = U + (int64_t)mu * link_plane_stride<T>(V);
+        m3<T> u;
+        load_link(plane, V, site_back(L, s, mu, c[mu]), u);  // U_mu(x - mu)
+        accumulate_link(u, (T)1, acc);
+        load_link(plane, V, s, u);  // - U_mu(x)
+        accumulate_link(u, (T)-1, acc);
+        fs += u.e[0].r + u.e[4].r + u.e[8].r;  // Re Tr U_mu(x)
+      }
+      // Delta_ij = acc (off-diagonal), Delta_ii = 2i (Im B_ii - mean)
+      const T m = (acc[6] + acc[7] + acc[8]) / (T)3;
+      const T a0 = 2 * (acc[6] - m), a1 = 2 * (acc[7] - m), a2 = 2 * (acc[8] - m);
+      const T ts = a0 * a0 + a1 * a1 + a2 * a2 +
+                   2 * (acc[0] * acc[0] + acc[1] * acc[1] + acc[2] * acc[2] + acc[3] * acc[3] + acc[4] * acc[4] +
+                        acc[5] * acc[5]);
+      th += widen_exact(ts);
+      f += widen_exact(fs);
+      st(P, s, mkc(convert<PT>(acc[0]), convert<PT>(acc[1])));
+      st(P, V + s, mkc(convert<PT>(acc[2]), convert<PT>(acc[3])));
+      st(P, 2 * V + s, mkc(convert<PT>(acc[4]), convert<PT>(acc[5])));
+      st(P, 3 * V + s, mkc(convert<PT>(a0), convert<PT>(a1)));
     }
-    // Delta_ij = acc (off-diagonal), Delta_ii = 2i (Im B_ii - mean)
-    const T m = (acc[6] + acc[7] + acc[8]) / (T)3;
-    const T a0 = 2 * (acc[6] - m), a1 = 2 * (acc[7] - m), a2 = 2 * (acc[8] - m);
-    const T ts = a0 * a0 + a1 * a1 + a2 * a2 +
-                 2 * (acc[0] * acc[0] + acc[1] * acc[1] + acc[2] * acc[2] + acc[3] * acc[3] + acc[4] * acc[4] +
-                      acc[5] * acc[5]);
-    th += (double)ts;
-    f += (double)fs;
-    st(P, s, mkc(convert<PT>(acc[0]), convert<PT>(acc[1])));
-    st(P, V + s, mkc(convert<PT>(acc[2]), convert<PT>(acc[3])));
-    st(P, 2 * V + s, mkc(convert<PT>(acc[4]), convert<PT>(acc[5])));
-    st(P, 3 * V + s, mkc(convert<PT>(a0), convert<PT>(a1)));
   }
   reduce_and_finalize<NT>(th, f, partials, ctrl, V, counts_update);
 }
