@@ -43,7 +43,7 @@ FP32_OPS_PER_CLK = 152 * 128         # 152 SMs x 128 FP32 lanes (one FADD, FMUL 
 # DRAM bytes (read + write) per launch of a kernel at 64^4, from one ncu capture of
 # dram__bytes_read.sum + dram__bytes_write.sum (profiles/gauge_update_f64_64x4_traffic.md); valid only
 # for the kernel version that was captured.
-TRAFFIC_64 = {"gauge_update.f64": 14.53e9 + 9.89e9}
+TRAFFIC_64 = {"gauge_update.f64": 14.53e9 + 9.86e9}
 
 
 def peaks():
@@ -76,8 +76,8 @@ def algorithmic(kernel, dims):
         "fft_z_fwd": (8 * es, 4 * 5 * lg["z"]), "fft_z_inv": (8 * es, 4 * 5 * lg["z"]),
         "fft_zt_filter": (8 * es, 4 * (2 * 5 * (lg["z"] + lg["t"]) + 6)),
         "fft_t_filter": (8 * es, 4 * (2 * 5 * lg["t"] + 6)),
-        # packed Delta-tilde read, g written
-        "gauge_g": ((4 + 9) * es, 160),
+        # packed Delta-tilde read, g written (double path: also a = g - 1 in double-float, 9 x 16 B)
+        "gauge_g": ((4 + 9 + (9 if prec == "f64" else 0)) * es, 160),
         # links read and written, g read (neighbours are the same data). Double: the small-step form,
         # which every warp of the double stage takes: per link, rows 0-1 of two 3x3 complex products in
         # double-float, 6 outputs x 3 terms x 4 real products x 2 = 144 multiply-accumulates of 12 FP32

@@ -83,6 +83,7 @@ template <typename T> struct State {
   T *U = nullptr;  // links, planes
   T *P = nullptr;  // packed Delta / Delta-tilde, 4 planes
   T *G = nullptr;  // g, 9 planes
+  float *A = nullptr;  // double path: a = g - 1 in double-float, 9 planes of float4
   void *tw[4] = {nullptr, nullptr, nullptr, nullptr};
   std::vector<Pass> passes;
   FFTTables tables;
@@ -447,6 +448,7 @@ template <typename T> lgf_status setup_precision(lgf_ctx *ctx, State<T> &S) {
   TRY(alloc(ctx, &S.U, nb * 4 * LinkStore<T>::planes * V * 2));
   TRY(alloc(ctx, &S.P, nb * 4 * V * 2));
   TRY(alloc(ctx, &S.G, nb * 9 * V * 2));
+  if constexpr (std::is_same<T, double>::value) TRY(alloc(ctx, &S.A, nb * 9 * V * 4));
   if (!S.tw[0]) {
     for (int mu = 0; mu < 4; ++mu) {
       const int N = ctx->n[mu];
@@ -593,7 +595,7 @@ template <typename T> lgf_status launch_gauge(lgf_ctx *ctx, State<T> &S, double 
   TRY(with_fft_type<T>(ctx, [&](auto tag) -> lgf_status {
     using FT = decltype(tag);
     k_gauge<T, NT, FT><<<dim3(grid1(ctx->V, NT), 1, ctx->nb), NT, 0, ctx->stream>>>(
-        reinterpret_cast<const FT *>(S.P), S.G, (T)(0.5 * alpha), ctx->V, ctx->ctrl, check_active, kid<T>(KID_GAUGE),
+        reinterpret_cast<const FT *>(S.P), S.G, S.A, (T)(0.5 * alpha), ctx->V, ctx->ctrl, check_active, kid<T>(KID_GAUGE),
         ctx->small_step ? 1 : 0);
     CKL();
     return LGF_OK;
@@ -606,9 +608,9 @@ template <typename T> lgf_status launch_update(lgf_ctx *ctx, State<T> &S, int ch
   if constexpr (std::is_same<T, double>::value) {
     k_update<double, NT_UPDATE64><<<dim3(grid1(ctx->V, NT_UPDATE64), 1, ctx->nb), NT_UPDATE64,
                                     update_smem_bytes<NT_UPDATE64>(), ctx->stream>>>(
-        S.U, S.G, ctx->L, ctx->ctrl, check_active, kid<T>(KID_UPDATE), ctx->small_step ? 1 : 0);
+        S.U, S.G, S.A, ctx->L, ctx->ctrl, check_active, kid<T>(KID_UPDATE), ctx->small_step ? 1 : 0);
   } else {
-    k_update<T, NT><<<dim3(grid1(ctx->V, NT), 1, ctx->nb), NT, 0, ctx->stream>>>(S.U, S.G, ctx->L, ctx->ctrl,
+    k_update<T, NT><<<dim3(grid1(ctx->V, NT), 1, ctx->nb), NT, 0, ctx->stream>>>(S.U, S.G, nullptr, ctx->L, ctx->ctrl,
                                                                                check_active, kid<T>(KID_UPDATE), 0);
   }
   CKL();
@@ -636,7 +638,8 @@ lgf_status launch_iteration_fft32(lgf_ctx *ctx, double alpha) {
   TRY(launch_filter<float>(ctx, ctx->s32, ctx->s32.P, 2));
   TRY(timed_begin(ctx, kid<double>(KID_GAUGE)));
   k_gauge<double, NT, float><<<dim3(grid1(ctx->V, NT), 1, ctx->nb), NT, 0, ctx->stream>>>(
-      ctx->s32.P, ctx->s64.G, 0.5 * alpha, ctx->V, ctx->ctrl, 1, kid<double>(KID_GAUGE), ctx->small_step ? 1 : 0);
+      ctx->s32.P, ctx->s64.G, ctx->s64.A, 0.5 * alpha, ctx->V, ctx->ctrl, 1, kid<double>(KID_GAUGE),
+      ctx->small_step ? 1 : 0);
   CKL();
   TRY(timed_end(ctx));
   TRY(launch_update<double>(ctx, ctx->s64, 1));
@@ -836,6 +839,7 @@ void lgf_destroy(lgf_ctx *ctx) {
   fr(ctx->s64.U);
   fr(ctx->s64.P);
   fr(ctx->s64.G);
+  fr(ctx->s64.A);
   fr(ctx->s32.U);
   fr(ctx->s32.P);
   fr(ctx->s32.G);
@@ -1172,7 +1176,7 @@ template <typename T> static lgf_status step_gauge(lgf_ctx *ctx, State<T> &S, co
     k_pack_antiherm<double><<<grid1(V, NT), NT, 0, ctx->stream>>>(src, S.P, V);
     CKL();
     k_gauge<double, NT, double><<<dim3(grid1(V, NT), 1, 1), NT, 0, ctx->stream>>>(
-        S.P, S.G, 0.5 * alpha, V, ctx->ctrl, 0, kid<T>(KID_GAUGE), ctx->small_step ? 1 : 0);
+        S.P, S.G, S.A, 0.5 * alpha, V, ctx->ctrl, 0, kid<T>(KID_GAUGE), ctx->small_step ? 1 : 0);
     CKL();
   } else {
     TRY(pack_field<T>(ctx, S, src));
@@ -1212,6 +1216,10 @@ template <typename T> static lgf_status step_update(lgf_ctx *ctx, State<T> &S, c
   CKL();
   k_aos_to_planes<T><<<grid1(V, NT), NT, 0, ctx->stream>>>(gsrc, S.G, V, 1, 9);
   CKL();
+  if constexpr (std::is_same<T, double>::value) {
+    k_a_from_g<NT><<<grid1(V, NT), NT, 0, ctx->stream>>>(S.G, S.A, V);
+    CKL();
+  }
   TRY(launch_update<T>(ctx, S, 0));
   k_planes_to_aos<T><<<grid1(4 * V, NT), NT, 0, ctx->stream>>>(S.U, dst, V, 4, LinkStore<T>::planes);
   CKL();

@@ -386,13 +386,25 @@ __device__ __forceinline__ void small_step_projection(const m3<df64> &X, m3<df64
   a.e[8] = conjg(a.e[0] * a.e[4] - a.e[1] * a.e[3] + a.e[4] + a.e[0]);
 }
 
+// The double path also stores a = g - 1 in double-float (A, 9 planes of float4): the small-step update
+// reads a and its neighbours' b = g(x+mu) - 1 from there without conversions.
+__device__ __forceinline__ void st_a(float *A, int64_t idx, cx<df64> v) {
+  reinterpret_cast<float4 *>(A)[idx] = to_vec<df64>(v);
+}
+__device__ __forceinline__ cx<df64> minus_identity_split(cx<double> v, int e) {
+  if (e == 0 || e == 4 || e == 8) v.r -= 1.0;  // exact for |g_ii - 1| <= 1/2 (Sterbenz)
+  return {df64_split_fast(v.r), df64_split_fast(v.i)};
+}
+
 template <typename T, int NT, typename PT = T>
-__global__ void __launch_bounds__(NT) k_gauge(const PT *__restrict__ P, T *__restrict__ G, T half_alpha, int64_t V,
-                                             const Ctrl *ctrl, int check_active, int tkid, int allow_small) {
+__global__ void __launch_bounds__(NT) k_gauge(const PT *__restrict__ P, T *__restrict__ G, float *__restrict__ A,
+                                             T half_alpha, int64_t V, const Ctrl *ctrl, int check_active, int tkid,
+                                             int allow_small) {
   {
     const int cfg = blockIdx.z;
     P += (int64_t)cfg * 4 * V * 2;
     G += (int64_t)cfg * 9 * V * 2;
+    if (A) A += (int64_t)cfg * 9 * V * 4;
     ctrl += cfg;
   }
   if (!should_run<T>(ctrl, check_active)) return;
@@ -413,6 +425,7 @@ __global__ void __launch_bounds__(NT) k_gauge(const PT *__restrict__ P, T *__res
         double re = convert<double>(a.e[e].r);
         if (e == 0 || e == 4 || e == 8) re = 1.0 + re;
         st(G, (int64_t)e * V + s, mkc(re, convert<double>(a.e[e].i)));
+        if (A) st_a(A, (int64_t)e * V + s, a.e[e]);
       }
       return;
     }
@@ -425,6 +438,20 @@ __global__ void __launch_bounds__(NT) k_gauge(const PT *__restrict__ P, T *__res
   reunitarize(g);
 #pragma unroll
   for (int e = 0; e < 9; ++e) st(G, (int64_t)e * V + s, g.e[e]);
+  if constexpr (std::is_same<T, double>::value) {
+    if (A) {
+#pragma unroll
+      for (int e = 0; e < 9; ++e) st_a(A, (int64_t)e * V + s, minus_identity_split(g.e[e], e));
+    }
+  }
+}
+
+// A = g - 1 in double-float from a g field (the single-step update takes g from the caller).
+template <int NT> __global__ void k_a_from_g(const double *__restrict__ G, float *__restrict__ A, int64_t V) {
+  const int64_t s = (int64_t)blockIdx.x * NT + threadIdx.x;
+  if (s >= V) return;
+#pragma unroll
+  for (int e = 0; e < 9; ++e) st_a(A, (int64_t)e * V + s, minus_identity_split(ldg(G, (int64_t)e * V + s), e));
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -440,16 +467,11 @@ __global__ void __launch_bounds__(NT) k_gauge(const PT *__restrict__ P, T *__res
 //    is far below the bound.
 //  * general step: rows 0 and 1 of g(x) U g^+(x+mu) by FP64 products, row 2 = conj(row0 x row1).
 // ---------------------------------------------------------------------------------------------
-constexpr int kSmallStepExpField = 1023 - 8;  // |x| < 2^-7  <=>  biased FP64 exponent <= 1015
+constexpr int kSmallStepFloatExpField = 127 - 8;  // |x| < 2^-7  <=>  float exponent field of hi <= 119
 
-__device__ __forceinline__ int exp_field(double x) {
-  return (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FF);
-}
-// Element e of g - 1 in double-float, and the largest exponent field of its parts so far.
-__device__ __forceinline__ cx<df64> minus_identity_df(cx<double> v, int e, int &emax) {
-  if (e == 0 || e == 4 || e == 8) v.r -= 1.0;  // exact for |g_ii - 1| <= 1/2 (Sterbenz)
-  emax = max(emax, max(exp_field(v.r), exp_field(v.i)));
-  return {df64_split_fast(v.r), df64_split_fast(v.i)};
+// Largest float exponent field of the high parts of a double-float complex element, with the running max.
+__device__ __forceinline__ int exp_max_df(cx<df64> v, int emax) {
+  return max(emax, max((int)((__float_as_uint(v.r.hi) >> 23) & 0xFF), (int)((__float_as_uint(v.i.hi) >> 23) & 0xFF)));
 }
 __device__ __forceinline__ cx<df64> dfc_add(cx<df64> x, cx<df64> y) { return {x.r + y.r, x.i + y.i}; }
 // (integer widening: the float -> double conversion instruction occupies the FP64 pipe)
@@ -465,19 +487,19 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // Shared memory of the double update per block of NT threads, [slot][thread] in 16-byte units:
-// a = g(x) - 1 in double-float (9 slots), two buffers of links (2 x 9), g(x+mu) (9).
+// a = g(x) - 1 (9 slots), two buffers of links (2 x 9), b = g(x+mu) - 1 (9), a and b in double-float.
 template <int NT> constexpr size_t update_smem_bytes() { return (size_t)36 * NT * 16; }
 
-// Start the copies of link mu at site s (9 elements to bu) and of g at its forward neighbour sf (to bg).
+// Start the copies of link mu at site s (9 elements to bu) and of b at its forward neighbour sf (to bb).
 template <int NT>
-__device__ __forceinline__ void fetch_link(const double *plane, const double *G, int64_t V, int64_t s, int64_t sf,
-                                           double2 *bu, double2 *bg) {
+__device__ __forceinline__ void fetch_link(const double *plane, const float *A, int64_t V, int64_t s, int64_t sf,
+                                           double2 *bu, float4 *bb) {
   const double2 *pu = reinterpret_cast<const double2 *>(plane);
-  const double2 *pg = reinterpret_cast<const double2 *>(G);
+  const float4 *pa = reinterpret_cast<const float4 *>(A);
 #pragma unroll
   for (int e = 0; e < 9; ++e) {
     cp_async16(bu + e * NT + threadIdx.x, pu + (int64_t)e * V + s);
-    cp_async16(bg + e * NT + threadIdx.x, pg + (int64_t)e * V + sf);
+    cp_async16(bb + e * NT + threadIdx.x, pa + (int64_t)e * V + sf);
   }
   cp_async_commit();
 }
@@ -542,11 +564,11 @@ __device__ __forceinline__ void update_link_small(double *plane, int64_t V, int6
   st(plane, 8 * V + s, cross_cj(r0[0], r1[1], r0[1], r1[0]));
 }
 
-// General-step update of one link in FP64: rows 0 and 1 of g(x) U g^+(x+mu) by products (g(x) from
-// global memory, the link from bu, g(x+mu) from bg), row 2 = conj(row0 x row1).
+// General-step update of one link in FP64: rows 0 and 1 of g(x) U g^+(x+mu) by products (g(x) and
+// g(x+mu) from global memory, the link from bu), row 2 = conj(row0 x row1).
 template <int NT>
 __device__ __forceinline__ void update_link_general(double *plane, const double *G, int64_t V, int64_t s,
-                                                    const double2 *bu, const double2 *bg) {
+                                                    int64_t sf, const double2 *bu) {
   m3<double> t;
 #pragma unroll
   for (int i = 0; i < 2; ++i) {
@@ -564,9 +586,9 @@ __device__ __forceinline__ void update_link_general(double *plane, const double 
   m3<double> o;
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
-    const cx<double> h0 = from_vec<double>(bg[(3 * j) * NT + threadIdx.x]);
-    const cx<double> h1 = from_vec<double>(bg[(3 * j + 1) * NT + threadIdx.x]);
-    const cx<double> h2 = from_vec<double>(bg[(3 * j + 2) * NT + threadIdx.x]);
+    const cx<double> h0 = ldg(G, (int64_t)(3 * j) * V + sf);
+    const cx<double> h1 = ldg(G, (int64_t)(3 * j + 1) * V + sf);
+    const cx<double> h2 = ldg(G, (int64_t)(3 * j + 2) * V + sf);
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
       cx<double> acc = {0, 0};
@@ -581,13 +603,14 @@ __device__ __forceinline__ void update_link_general(double *plane, const double 
 
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 3 : 2)
-    k_update(T *__restrict__ U, const T *__restrict__ G, Lattice L, const Ctrl *ctrl, int check_active, int tkid,
-             int allow_small) {
+    k_update(T *__restrict__ U, const T *__restrict__ G, const float *__restrict__ A, Lattice L, const Ctrl *ctrl,
+             int check_active, int tkid, int allow_small) {
   const int64_t V = L.V;
   {
     const int cfg = blockIdx.z;
     U += (int64_t)cfg * 4 * link_plane_stride<T>(V);
     G += (int64_t)cfg * 9 * V * 2;
+    if (A) A += (int64_t)cfg * 9 * V * 4;
     ctrl += cfg;
   }
   if (!should_run<T>(ctrl, check_active)) return;
@@ -602,13 +625,18 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 3 : 2)
     extern __shared__ __align__(16) unsigned char update_smem[];
     float4 *sa = reinterpret_cast<float4 *>(update_smem);
     double2 *bu0 = reinterpret_cast<double2 *>(sa + 9 * NT);
-    double2 *bg = bu0 + 18 * NT;
+    float4 *bb = reinterpret_cast<float4 *>(bu0 + 18 * NT);
     const int64_t pstride = link_plane_stride<T>(V);
-    fetch_link<NT>(U, G, V, s, site_fwd(L, s, 0, c[0]), bu0, bg);
+    {  // a = g(x) - 1 with the first link and b (one group of copies)
+      const float4 *pa = reinterpret_cast<const float4 *>(A);
+#pragma unroll
+      for (int e = 0; e < 9; ++e) cp_async16(sa + e * NT + threadIdx.x, pa + (int64_t)e * V + s);
+    }
+    fetch_link<NT>(U, A, V, s, site_fwd(L, s, 0, c[0]), bu0, bb);
+    cp_async_wait_all();
     int ea = 0;
 #pragma unroll
-    for (int e = 0; e < 9; ++e)
-      sa[e * NT + threadIdx.x] = to_vec<df64>(minus_identity_df(ldg(G, (int64_t)e * V + s), e, ea));
+    for (int e = 0; e < 9; ++e) ea = exp_max_df(from_vec<df64>(sa[e * NT + threadIdx.x]), ea);
 #pragma unroll 1
     for (int mu = 0; mu < 4; ++mu) {
       double *plane = U + (int64_t)mu * pstride;
@@ -617,8 +645,12 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 3 : 2)
       cx<df64> b[9];
       int eb = ea;
 #pragma unroll
-      for (int e = 0; e < 9; ++e) b[e] = minus_identity_df(from_vec<double>(bg[e * NT + threadIdx.x]), e, eb);
-      if (__all_sync(__activemask(), allow_small && eb <= kSmallStepExpField)) {
+      for (int e = 0; e < 9; ++e) {
+        b[e] = from_vec<df64>(bb[e * NT + threadIdx.x]);
+        eb = exp_max_df(b[e], eb);
+      }
+      const int64_t sf = site_fwd(L, s, mu, c[mu]);
+      if (__all_sync(__activemask(), allow_small && eb <= kSmallStepFloatExpField)) {
         cx<df64> u[9];
 #pragma unroll
         for (int e = 0; e < 9; ++e) {
@@ -626,14 +658,14 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 3 : 2)
           u[e] = {df64_split_fast(v.x), df64_split_fast(v.y)};
         }
         if (mu < 3)
-          fetch_link<NT>(plane + pstride, G, V, s, site_fwd(L, s, mu + 1, c[mu + 1]), bu0 + ((mu + 1) & 1) * 9 * NT,
-                         bg);
+          fetch_link<NT>(plane + pstride, A, V, s, site_fwd(L, s, mu + 1, c[mu + 1]), bu0 + ((mu + 1) & 1) * 9 * NT,
+                         bb);
         update_link_small<NT>(plane, V, s, sa, bu0 + (mu & 1) * 9 * NT, u, b);
       } else {
-        update_link_general<NT>(plane, G, V, s, bu, bg);
+        update_link_general<NT>(plane, G, V, s, sf, bu);
         if (mu < 3)
-          fetch_link<NT>(plane + pstride, G, V, s, site_fwd(L, s, mu + 1, c[mu + 1]), bu0 + ((mu + 1) & 1) * 9 * NT,
-                         bg);
+          fetch_link<NT>(plane + pstride, A, V, s, site_fwd(L, s, mu + 1, c[mu + 1]), bu0 + ((mu + 1) & 1) * 9 * NT,
+                         bb);
       }
     }
   } else {

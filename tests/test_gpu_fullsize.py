@@ -2,10 +2,10 @@
 
 32^4 (eps = 0.6, seed 2; and pure gauge): the oracle runs a few iterations of Algorithm 1 in seconds,
 so the first iterations are compared element by element, plus one-step parity from a mid-trajectory
-GPU state. 64^4 (eps = 0.6, seed 4, the mixed schedule the benchmark times): the oracle is too slow
-for a trajectory, so the fixed links are checked through quantities it computes in one pass (theta,
-F, plaquette, unitarity), and the Fourier filter through the identity -d^2 (filtered Delta) =
-p^2_max Delta at sampled sites, which holds at any size."""
+GPU state. 64^4 (eps = 0.6, seed 4, the mixed schedule the benchmark times, and the double path): the
+oracle is too slow for a trajectory, so the fixed links are checked through quantities it computes in one
+pass (theta, F, plaquette, unitarity), and the Fourier filter through the identity -d^2 (filtered
+Delta) = p^2_max Delta at sampled sites, which holds at any size."""
 import numpy as np
 import pytest
 
@@ -77,6 +77,34 @@ def test_64_4_mixed_fix_invariants(lgf):
     with lgf.Lattice(dims) as lat:
         r = lat.fix(Ud, 0.08, 1e-15, "mixed")
     assert r["converged"] and r["theta"] < 1e-15
+    Uf = Ud.cpu().numpy()
+    del Ud
+    D = oracle.delta(Uf)
+    th = oracle.theta(D)
+    del D
+    assert th < 1e-15 and abs(th - r["theta"]) <= theta_tol(r["theta"])
+    F = oracle.functional(Uf)
+    assert abs(F - r["F"]) <= 1e-12 * abs(F)
+    assert abs(oracle.plaquette(Uf) - plaq0) < 1e-14
+    assert oracle.unitarity_violation(Uf) < 1e-13
+
+
+def test_64_4_double_path_invariants_and_same_maximum(lgf):
+    """The double path at full size (its small-step forms run on every warp of the later iterations):
+    the oracle's theta, F, plaquette and unitarity of the fixed links; and the mixed schedule reaches the
+    same maximum of F on this field."""
+    dims = (64, 64, 64, 64)
+    U = synth.config(dims, 4, 0.6)
+    plaq0 = oracle.plaquette(U)
+    Ud = dev(U)
+    with lgf.Lattice(dims) as lat:
+        r = lat.fix(Ud, 0.08, 1e-15, "fp64")
+        Um = dev(U)
+        del U
+        rm = lat.fix(Um, 0.08, 1e-15, "mixed")
+        del Um
+    assert r["converged"] and r["theta"] < 1e-15
+    assert rm["converged"] and abs(rm["F"] - r["F"]) <= 1e-12 * abs(r["F"])
     Uf = Ud.cpu().numpy()
     del Ud
     D = oracle.delta(Uf)
