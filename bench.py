@@ -156,6 +156,25 @@ def dist_env():
     return ws, rank, local
 
 
+def replica_seed(seed, rank):
+    """Each rank fixes its own configuration, a replica: the generator seed is offset by the rank."""
+    return seed + rank
+
+
+def reduce_over_ranks(ms, work, ws, device):
+    """Whole-job figures over independent replicas: the slowest rank's time and the summed work
+    (site-iterations). The only collective of the bench; none is on the data path."""
+    if ws == 1:
+        return ms, work
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    w = torch.tensor([float(work)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(w[0])
+
+
 def run_reference(args, dims, rank, ws):
     """The FP64 CPU oracle on the host cores: each step is one iteration of Algorithm 1 on the 64^4
     configuration (the untimed part loads the configuration and its initial Delta)."""
@@ -370,7 +389,7 @@ def main():
     import paper_1210_8018_gb300 as lgf
 
     V = int(np.prod(dims))
-    seed = args.seed + rank
+    seed = replica_seed(args.seed, rank)
     host = torch.empty(synth.links_shape(dims), dtype=torch.complex128).pin_memory()
     synth.config(dims, seed, args.eps, out=host.numpy())
     U_in = host.to("cuda", non_blocking=False)
@@ -409,14 +428,7 @@ def main():
         barrier()
     ktimes = lat.kernel_times()
     ms = ev0.elapsed_time(ev1)
-    t_max = ms
-    site_iters = V * sum(iters)
-    if ws > 1:
-        t = torch.tensor([ms, float(site_iters)], device="cuda", dtype=torch.float64)
-        tm = t.clone()
-        torch.distributed.all_reduce(tm[:1], op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
-        t_max, site_iters = float(tm[0]), float(t[1])
+    t_max, site_iters = reduce_over_ranks(ms, V * sum(iters), ws, "cuda")
     value = site_iters / (t_max / 1e3)
     lat.enable_timing(False)
 
@@ -507,9 +519,10 @@ def main():
             if rep > 0:
                 times.append((dt, r["iters"]))
         dt, it = times[0]
-        nbytes = 4 * V * 144
-        e2e = {"value": V * it / dt, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
-               "time_to_theta_s": dt, "step": "one lgf_fix call on pinned host links"}
+        dt_max, work = reduce_over_ranks(dt, V * it, ws, "cuda")
+        nbytes = 4 * V * 144 * ws  # every rank copies its own links in and out
+        e2e = {"value": work / dt_max, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+               "time_to_theta_s": dt_max, "step": "one lgf_fix call on pinned host links"}
 
     if rank == 0:
         gpu_launches = sum(v[0] for v in ktimes.values())
