@@ -54,11 +54,11 @@ def peaks():
     return 6800.0, 2070.0, "fallback"
 
 
-def algorithmic(kernel, dims):
-    """Algorithmic bytes and arithmetic per launch of each kernel (each datum counted once).
-    es = bytes per complex number. The arithmetic is (count, kind): kind "fp64" counts FP64 flops (FMA = 2),
-    kind "fp32" counts FP32-pipe operations (FADD, FMUL, FFMA = 1 each), None when the kernel is modelled by
-    its bytes only."""
+def work_model(kernel, dims):
+    """Algorithmic bytes and arithmetic per launch of each kernel (each datum counted once), and the
+    precision of the kernel: (bytes, count, prec). es = bytes per complex number. The count is in the units
+    of algorithmic(): FP64 flops (FMA = 2), FP32-pipe operations, or, for the FFT passes, the flop
+    convention of the paper (5 N log2 N per axis, field and direction)."""
     V = int(np.prod(dims))
     name, prec = kernel.rsplit(".", 1)
     es = 16 if prec == "f64" else 8
@@ -95,11 +95,20 @@ def algorithmic(kernel, dims):
         "set_identity": (6 * 8, 0),
     }
     b, f = table[name]
+    return b * V, f * V, prec
+
+
+def algorithmic(kernel, dims):
+    """Bytes and arithmetic per launch for the roofline: (bytes, count, kind) with kind "fp64" (FP64 flops,
+    FMA = 2), "fp32" (FP32-pipe operations: FADD, FMUL, FFMA = 1 each) or None (the kernel is modelled by
+    its bytes only; count 0)."""
+    b, f, prec = work_model(kernel, dims)
+    name = kernel.rsplit(".", 1)[0]
     if prec == "f64":
         kind = {"gauge_update": "fp32", "handover_transform": "fp64", "gacc_to_double": "fp64"}.get(name)
     else:
         kind = "fp64" if name == "gauge_update_fused_reunit" else None
-    return b * V, (f * V if kind else 0), kind
+    return b, (f if kind else 0), kind
 
 
 class ClockSampler:

@@ -114,6 +114,32 @@ def test_trajectory_fp64(lgf, dims, seed, eps):
     assert_matrix_close(Ud.cpu().numpy(), Uo, rtol=1e-11)
 
 
+@pytest.mark.parametrize("dims,seed,eps", [((8, 8, 8, 8), 1, 0.3), ((6, 4, 8, 10), 5, 0.6)])
+def test_trajectory_plain_ieee_double_forms(lgf, dims, seed, eps, monkeypatch):
+    """The double path with every step in plain IEEE double (the Fourier filter in double instead of
+    double-float, no small-step forms): the same trajectory parity as the default forms, and the filter
+    step itself."""
+    monkeypatch.setenv("LGF_FFT_NATIVE_F64", "1")
+    monkeypatch.setenv("LGF_SMALL_STEP", "0")
+    U = synth.config(dims, seed, eps)
+    D = oracle.delta(U)
+    Dt_ref = oracle.fourier_filter(D)
+    Uo, it_o, th_o, F_o, h_o = oracle.fix(U, 0.08, 1e-15, 2000, hist_len=2001)
+    Ud = dev(U)
+    with lgf.Lattice(dims) as lat:
+        out = np.empty_like(D)
+        lat.filter(D, out)
+        r = lat.fix(Ud, 0.08, 1e-15, "fp64", history_len=2001)
+    assert_matrix_close(out, Dt_ref, scale=float(np.abs(Dt_ref).max()))
+    assert r["converged"] and r["theta"] < 1e-15
+    assert abs(r["iters"] - it_o) <= 1
+    h_g = r["history"]
+    for k in range(min(len(h_g), len(h_o))):
+        assert abs(h_g[k, 1] - h_o[k, 1]) <= 1e-12 * abs(h_o[k, 1]), (k, h_g[k], h_o[k])
+        assert abs(h_g[k, 0] - h_o[k, 0]) <= theta_tol(h_o[k, 0]), (k, h_g[k], h_o[k])
+    assert_matrix_close(Ud.cpu().numpy(), Uo, rtol=1e-11)
+
+
 def test_one_step_parity_after_iterations(lgf):
     """Run k GPU iterations, hand the GPU's links to the oracle and compare one more iteration."""
     dims = (8, 6, 4, 10)
