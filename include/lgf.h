@@ -69,8 +69,9 @@ typedef struct {
 void lgf_default_options(lgf_options *opt);
 
 /* Create a context for an Nx x Ny x Nz x Nt lattice on the current CUDA device. Every extent must be
- * >= 2 and a product of the primes 2, 3 and 5, and at most 1024. Device memory is allocated lazily by
- * the first call that needs it. Returns LGF_EINVAL for unsupported extents, LGF_ECUDA if no device.
+ * >= 2 and a product of the primes 2, 3 and 5, and at most 1024, and the volume must be below 2^31
+ * sites. Device memory is allocated lazily by the first call that needs it. Returns LGF_EINVAL for
+ * unsupported extents, LGF_ECUDA if no device.
  * Environment switches read here, each selecting an equivalent form of a step (all pass the same
  * tests): LGF_GENERIC_FFT=1 uses the generic FFT passes for every extent; LGF_FFT_NATIVE_F64=1 runs
  * the Fourier filter of the double path in IEEE double instead of double-float; and LGF_SMALL_STEP=0

@@ -772,6 +772,10 @@ static lgf_status create_ctx(const int n[4], int nb, lgf_ctx **out) {
   for (int mu = 0; mu < 4; ++mu)
     if (!factor_ok(n[mu]))
       return fail(nullptr, LGF_EINVAL, "lattice extents must be in [2, 1024] and products of 2, 3 and 5");
+  // site indices are decomposed with 32-bit arithmetic in the kernels (such a lattice needs over 1 TB of
+  // links in any case)
+  if ((int64_t)Nx * Ny * Nz * Nt >= ((int64_t)1 << 31))
+    return fail(nullptr, LGF_EINVAL, "the lattice volume must be below 2^31 sites");
   lgf_ctx *ctx = new lgf_ctx();
   ctx->nb = nb;
   for (int mu = 0; mu < 4; ++mu) ctx->n[mu] = n[mu];

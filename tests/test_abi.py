@@ -56,6 +56,17 @@ def test_host_only_calls(lib):
     assert isinstance(lgf._lib.lgf_last_error(None), bytes)
 
 
+def test_create_rejects_bad_extents_before_any_device_call(lib):
+    """Extent checks happen before the context touches CUDA, so they run on a machine without a GPU."""
+    lib.lgf_create.argtypes = [ctypes.c_int] * 4 + [ctypes.POINTER(ctypes.c_void_p)]
+    lib.lgf_last_error.restype = ctypes.c_char_p
+    h = ctypes.c_void_p()
+    for dims in [(7, 4, 4, 4), (1, 4, 4, 4), (2048, 4, 4, 4), (1024, 1024, 1024, 2)]:
+        assert lib.lgf_create(*dims, ctypes.byref(h)) == 1  # LGF_EINVAL
+        assert not h.value
+    assert b"2^31" in lib.lgf_last_error(None)
+
+
 def test_no_oracle_in_product_path():
     """The product path (package and library sources) never refers to the oracle."""
     for path in glob.glob(os.path.join(ROOT, "paper_1210_8018_gb300", "**", "*"), recursive=True):
