@@ -509,7 +509,9 @@ bool is_device_ptr(const void *p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-// Resolve a caller buffer of `bytes` to a device pointer, staging host data through `buf`.
+// Resolve a caller buffer of `bytes` to a device pointer: device memory as it is, host memory staged
+// through `buf` by the copy engine (measured faster than kernels reading page-locked host memory over
+// the host link).
 lgf_status input_ptr(lgf_ctx *ctx, const double *p, size_t bytes, double **buf, size_t *have, const double **out) {
   if (!p) return fail(ctx, LGF_EINVAL, "null buffer");
   if (is_device_ptr(p)) {
@@ -905,10 +907,17 @@ lgf_status lgf_load(lgf_ctx *ctx, const double *links, int precision) {
     TRY(setup_precision<float>(ctx, ctx->s32));
     TRY(alloc(ctx, &ctx->Gacc, (size_t)ctx->nb * 6 * V * 2));
     if (precision == LGF_MIXED) {
+      // the caller's links are read once: into the double planes kept for the handover, and the float
+      // links from those
       TRY(alloc(ctx, &ctx->U0, (size_t)ctx->nb * 4 * 9 * V * 2));
       TRY(to_planes<double>(ctx, src, ctx->U0, 4));
+      TRY(timed_begin(ctx, kid<float>(KID_TO_PLANES)));
+      k_narrow_link_planes<<<grid1((int64_t)4 * V, NT), NT, 0, ctx->stream>>>(ctx->U0, ctx->s32.U, V);
+      CKL();
+      TRY(timed_end(ctx));
+    } else {
+      TRY(to_planes<float>(ctx, src, ctx->s32.U, 4));
     }
-    TRY(to_planes<float>(ctx, src, ctx->s32.U, 4));
     TRY(timed_begin(ctx, kid<float>(KID_SET_IDENTITY)));
     k_set_identity<<<grid1(V, NT), NT, 0, ctx->stream>>>(ctx->Gacc, V);
     CKL();

@@ -71,6 +71,19 @@ __global__ void __launch_bounds__(NT) k_update_fused_f32(float *__restrict__ U, 
   }
 }
 
+// Float links (rows 0 and 1, 6 planes per direction) from the double link planes (9 per direction),
+// rounded to nearest.
+__global__ void k_narrow_link_planes(const double *__restrict__ U64, float *__restrict__ U32, int64_t V) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= 4 * V) return;
+  const int64_t mu = idx / V, s = idx - mu * V;
+#pragma unroll
+  for (int e = 0; e < 6; ++e) {
+    const cx<double> v = ldg(U64, (mu * 9 + e) * V + s);
+    st(U32, (mu * 6 + e) * V + s, mkc(narrow_bits(v.r), narrow_bits(v.i)));
+  }
+}
+
 // G64 = SU(3)-projection (in double) of the float accumulation.
 template <int NT>
 __global__ void __launch_bounds__(NT) k_gacc_to_double(const float *__restrict__ Gacc, double *__restrict__ G64,

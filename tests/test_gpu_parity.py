@@ -140,6 +140,25 @@ def test_trajectory_plain_ieee_double_forms(lgf, dims, seed, eps, monkeypatch):
     assert_matrix_close(Ud.cpu().numpy(), Uo, rtol=1e-11)
 
 
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_host_links_give_the_device_result(lgf, precision):
+    """Page-locked and pageable host links (staged through the context's buffers) give bitwise the result
+    of the same fix on device links."""
+    import torch
+    dims = (8, 8, 8, 8)
+    U = synth.config(dims, 2, 0.6)
+    pinned = torch.from_numpy(U.copy()).pin_memory()
+    pageable = U.copy()
+    Ud = dev(U)
+    with lgf.Lattice(dims) as lat:
+        r_dev = lat.fix(Ud, 0.08, 1e-15, precision)
+        r_pin = lat.fix(pinned.numpy(), 0.08, 1e-15, precision)
+        r_pag = lat.fix(pageable, 0.08, 1e-15, precision)
+    ref = Ud.cpu().numpy()
+    assert r_dev["iters"] == r_pin["iters"] == r_pag["iters"]
+    assert np.array_equal(pinned.numpy(), ref) and np.array_equal(pageable, ref)
+
+
 def test_one_step_parity_after_iterations(lgf):
     """Run k GPU iterations, hand the GPU's links to the oracle and compare one more iteration."""
     dims = (8, 6, 4, 10)
