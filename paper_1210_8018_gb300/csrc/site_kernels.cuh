@@ -6,7 +6,8 @@
 //   links  U[(mu*P + e)*V + s]   mu = 0..3, e = 3*row + col; P = 9 planes in double, P = 6 in float
 //          (rows 0 and 1 only: the float stage is bound by memory traffic, so row 2 is rebuilt as
 //          conj(row0 x row1) when a link is loaded -- the paper's "12 real" storage, Table 1)
-//   g      G[e*V + s]
+//   g      G[e*V + s]; in the double path also a = g - 1 in double-float, A[e*V + s] as float4
+//          (hi, lo of the real part, hi, lo of the imaginary part), read by the small-step update
 //   packed Delta (and Delta-tilde) P[f*V + s], f = 0..3:
 //     P0 = Delta_01, P1 = Delta_02, P2 = Delta_12, P3 = Im Delta_00 + i Im Delta_11.
 //   Delta is anti-Hermitian and traceless, so these 8 reals determine it; the Fourier filter is real

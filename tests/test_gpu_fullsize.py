@@ -3,9 +3,10 @@
 32^4 (eps = 0.6, seed 2; and pure gauge): the oracle runs a few iterations of Algorithm 1 in seconds,
 so the first iterations are compared element by element, plus one-step parity from a mid-trajectory
 GPU state. 64^4 (eps = 0.6, seed 4, the mixed schedule the benchmark times, and the double path): the
-oracle is too slow for a trajectory, so the fixed links are checked through quantities it computes in one
-pass (theta, F, plaquette, unitarity), and the Fourier filter through the identity -d^2 (filtered
-Delta) = p^2_max Delta at sampled sites, which holds at any size."""
+oracle is too slow for a whole trajectory, so it runs the first two iterations and one iteration from the
+mixed schedule's handover state; the fixed links are checked through quantities it computes in one pass
+(theta, F, plaquette, unitarity), and the Fourier filter through the identity -d^2 (filtered Delta) =
+p^2_max Delta at sampled sites, which holds at any size."""
 import numpy as np
 import pytest
 
@@ -115,6 +116,37 @@ def test_64_4_double_path_invariants_and_same_maximum(lgf):
     assert abs(F - r["F"]) <= 1e-12 * abs(F)
     assert abs(oracle.plaquette(Uf) - plaq0) < 1e-14
     assert oracle.unitarity_violation(Uf) < 1e-13
+
+
+def test_64_4_first_iterations_and_one_step_from_the_handover(lgf):
+    """At the benchmarked size and configuration: theta and F of the first two double-path iterations
+    against the oracle's; and one double-path iteration, element by element, from the mixed schedule's
+    state at the handover (theta <= 1e-8, where its double stage starts and every warp takes the small-step
+    forms)."""
+    dims = (64, 64, 64, 64)
+    U = synth.config(dims, 4, 0.6)
+    _, _, _, _, h_o = oracle.fix(U, 0.08, 0.0, 2, hist_len=3)
+    with lgf.Lattice(dims) as lat:
+        lat.load(U, "fp64")
+        r = lat.iterate(2, 0.08, 0.0, history_len=3)
+        for k in range(3):
+            assert abs(r["history"][k, 1] - h_o[k, 1]) <= 1e-12 * abs(h_o[k, 1]), (k, r["history"][k], h_o[k])
+            assert abs(r["history"][k, 0] - h_o[k, 0]) <= theta_tol(h_o[k, 0]), (k, r["history"][k], h_o[k])
+        lat.load(U, "mixed")
+        rh = lat.iterate(1 << 30, 0.08, 1e-8)  # stops at the handover: theta < 1e-8 in the double stage
+        assert rh["theta"] < 1e-8
+        del U
+        Uh = np.empty(synth.links_shape(dims), dtype=np.complex128)
+        lat.store(Uh)
+        lat.load(Uh, "fp64")
+        r1 = lat.iterate(1, 0.08, 0.0)
+        U1 = np.empty_like(Uh)
+        lat.store(U1)
+    Uo, _, th_o, F_o, _ = oracle.fix(Uh, 0.08, 0.0, 1, hist_len=2)
+    del Uh
+    assert_matrix_close(U1, Uo)
+    assert abs(r1["F"] - F_o) <= 1e-12 * abs(F_o)
+    assert abs(r1["theta"] - th_o) <= theta_tol(th_o)
 
 
 def test_64_4_filter_laplacian_identity_sampled(lgf):
