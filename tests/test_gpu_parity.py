@@ -159,6 +159,31 @@ def test_host_links_give_the_device_result(lgf, precision):
     assert np.array_equal(pinned.numpy(), ref) and np.array_equal(pageable, ref)
 
 
+def test_work_is_ordered_after_torchs_current_stream(lgf):
+    """With torch tensors the library issues its work on torch's current stream, after what torch queued
+    there: links produced on a side stream by a slow chain of kernels (zeros until the last one adds the
+    configuration) are fixed as if they had been ready."""
+    import torch
+    dims = (32, 32, 16, 16)
+    U = synth.config(dims, 3, 0.6)
+    ref = dev(U)
+    with lgf.Lattice(dims) as lat:
+        r_ref = lat.fix(ref, 0.08, 1e-15, "mixed")
+    src = dev(U)
+    s = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        Us = torch.zeros_like(src)
+        for _ in range(60):
+            Us.mul_(1.0)
+        Us.add_(src)
+        with lgf.Lattice(dims) as lat:
+            r = lat.fix(Us, 0.08, 1e-15, "mixed")
+        out = Us.clone()
+    torch.cuda.synchronize()
+    assert r["iters"] == r_ref["iters"] and torch.equal(out, ref)
+
+
 def test_one_step_parity_after_iterations(lgf):
     """Run k GPU iterations, hand the GPU's links to the oracle and compare one more iteration."""
     dims = (8, 6, 4, 10)
