@@ -43,7 +43,7 @@ FP32_OPS_PER_CLK = 152 * 128         # 152 SMs x 128 FP32 lanes (one FADD, FMUL 
 # DRAM bytes (read + write) per launch of a kernel at 64^4, from one ncu capture of
 # dram__bytes_read.sum + dram__bytes_write.sum (profiles/gauge_update_f64_64x4_traffic.md); valid only
 # for the kernel version that was captured.
-TRAFFIC_64 = {"gauge_update.f64": 14.53e9 + 9.86e9}
+TRAFFIC_64 = {"gauge_update.f64": 14.54e9 + 10.12e9}
 
 
 def peaks():
@@ -52,6 +52,14 @@ def peaks():
         p = json.load(open(path))
         return float(p["hbm_gbs"]), float(p.get("sm_max_mhz", 2070.0)), "measured"
     return 6800.0, 2070.0, "fallback"
+
+
+# Flops (multiply and add = 1 each, an FMA = 2) of the SU(3) arithmetic, counted from the source:
+# the projection onto SU(3) (two row norms 11 each, two row scalings 6 each, the overlap <r0, r1> 24, its
+# removal 24, the row-2 cross product 42; the two reciprocal square roots are not counted), and the
+# product g U g^+ kept as rows 0-1 of g U (132) and of (g U) g^+ (144) plus the row-2 cross product (42).
+PROJECTION_FLOP = 11 + 6 + 24 + 24 + 11 + 6 + 42
+LINK_PRODUCT_FLOP = 132 + 144 + 42
 
 
 def work_model(kernel, dims):
@@ -82,14 +90,14 @@ def work_model(kernel, dims):
         # which every warp of the double stage takes: per link, rows 0-1 of two 3x3 complex products in
         # double-float, 6 outputs x 3 terms x 4 real products x 2 = 144 multiply-accumulates of 12 FP32
         # operations each (Dot2 step); row 2 by an FP64 cross product (not counted). Float (plain FP32
-        # schedule): rows 0-1 of g U and of (g U) g^+, row 2 by a cross product, 336 flop.
-        "gauge_update": ((4 * lp * 2 + 9) * es, 4 * 144 * 12 if prec == "f64" else 4 * 336),
+        # schedule): rows 0-1 of g U (132 flop) and of (g U) g^+ (144), row 2 by a cross product (42).
+        "gauge_update": ((4 * lp * 2 + 9) * es, 4 * 144 * 12 if prec == "f64" else 4 * LINK_PRODUCT_FLOP),
         # float stage: links read and written, G read and written (rows 0-1), packed Delta-tilde read (g is
         # rebuilt in registers); the _reunit variant also projects the new links in double precision
         "gauge_update_fused": ((4 * lp * 2 + 12 + 4) * es, 0),
-        "gauge_update_fused_reunit": ((4 * lp * 2 + 12 + 4) * es, 4 * 170),
-        "gacc_to_double": (6 * 8 + 9 * 16, 170),
-        "handover_transform": (36 * 16 * 2 + 9 * 16, 4 * 336),
+        "gauge_update_fused_reunit": ((4 * lp * 2 + 12 + 4) * es, 4 * PROJECTION_FLOP),
+        "gacc_to_double": (6 * 8 + 9 * 16, PROJECTION_FLOP),
+        "handover_transform": (36 * 16 * 2 + 9 * 16, 4 * LINK_PRODUCT_FLOP),
         "to_planes": (4 * lp * 16 + 4 * lp * es, 0),  # the float load reads rows 0-1 of each link only
         "from_planes": (4 * lp * es + 36 * 16, 0),
         "set_identity": (6 * 8, 0),

@@ -29,8 +29,8 @@ using namespace lgf;
 namespace {
 
 constexpr int NT = 256;  // threads per block of the per-site kernels
-// threads per block of the double gauge update: its links and g(x+mu) are staged in 72 KB of shared
-// memory per block (three blocks per SM)
+// threads per block of the double gauge update: a, the link and b are staged in 54 KB of shared memory
+// per block (four blocks per SM)
 constexpr int NT_UPDATE64 = 128;
 
 enum KernelId {

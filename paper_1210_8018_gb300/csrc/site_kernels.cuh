@@ -488,9 +488,24 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // Shared memory of the double update per block of NT threads, [slot][thread] in 16-byte units:
-// a = g(x) - 1 (9 slots), two buffers of links (2 x 9), b = g(x+mu) - 1 (9), a and b in double-float.
-template <int NT> constexpr size_t update_smem_bytes() { return (size_t)36 * NT * 16; }
+// a = g(x) - 1 (9 slots), the link (9), b = g(x+mu) - 1 (9), a and b in double-float: 432 B per thread,
+// so that four blocks of 128 threads (16 warps) fit on an SM.
+template <int NT> constexpr size_t update_smem_bytes() { return (size_t)27 * NT * 16; }
 
+template <int NT>
+__device__ __forceinline__ void fetch_u(const double *plane, int64_t V, int64_t s, double2 *bu) {
+  const double2 *pu = reinterpret_cast<const double2 *>(plane);
+#pragma unroll
+  for (int e = 0; e < 9; ++e) cp_async16(bu + e * NT + threadIdx.x, pu + (int64_t)e * V + s);
+  cp_async_commit();
+}
+template <int NT>
+__device__ __forceinline__ void fetch_b(const float *A, int64_t V, int64_t sf, float4 *bb) {
+  const float4 *pa = reinterpret_cast<const float4 *>(A);
+#pragma unroll
+  for (int e = 0; e < 9; ++e) cp_async16(bb + e * NT + threadIdx.x, pa + (int64_t)e * V + sf);
+  cp_async_commit();
+}
 // Start the copies of link mu at site s (9 elements to bu) and of b at its forward neighbour sf (to bb).
 template <int NT>
 __device__ __forceinline__ void fetch_link(const double *plane, const float *A, int64_t V, int64_t s, int64_t sf,
@@ -603,7 +618,7 @@ __device__ __forceinline__ void update_link_general(double *plane, const double 
 }
 
 template <typename T, int NT>
-__global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 3 : 2)
+__global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 4 : 2)
     k_update(T *__restrict__ U, const T *__restrict__ G, const float *__restrict__ A, Lattice L, const Ctrl *ctrl,
              int check_active, int tkid, int allow_small) {
   const int64_t V = L.V;
@@ -621,12 +636,12 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 3 : 2)
   int c[4];
   site_coords(L, s, c);
   if constexpr (std::is_same<T, double>::value) {
-    // The copies of link mu + 1 run while link mu is computed (dynamic shared memory of
-    // update_smem_bytes<NT>()).
+    // b of link mu + 1 is copied while link mu is computed, the link itself once link mu is stored
+    // (dynamic shared memory of update_smem_bytes<NT>()); 16 resident warps cover that latency.
     extern __shared__ __align__(16) unsigned char update_smem[];
     float4 *sa = reinterpret_cast<float4 *>(update_smem);
     double2 *bu0 = reinterpret_cast<double2 *>(sa + 9 * NT);
-    float4 *bb = reinterpret_cast<float4 *>(bu0 + 18 * NT);
+    float4 *bb = reinterpret_cast<float4 *>(bu0 + 9 * NT);
     const int64_t pstride = link_plane_stride<T>(V);
     {  // a = g(x) - 1 with the first link and b (one group of copies)
       const float4 *pa = reinterpret_cast<const float4 *>(A);
@@ -641,7 +656,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 3 : 2)
 #pragma unroll 1
     for (int mu = 0; mu < 4; ++mu) {
       double *plane = U + (int64_t)mu * pstride;
-      const double2 *bu = bu0 + (mu & 1) * 9 * NT;
+      const double2 *bu = bu0;
       cp_async_wait_all();
       cx<df64> b[9];
       int eb = ea;
@@ -658,15 +673,12 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 3 : 2)
           const double2 v = bu[e * NT + threadIdx.x];
           u[e] = {df64_split_fast(v.x), df64_split_fast(v.y)};
         }
-        if (mu < 3)
-          fetch_link<NT>(plane + pstride, A, V, s, site_fwd(L, s, mu + 1, c[mu + 1]), bu0 + ((mu + 1) & 1) * 9 * NT,
-                         bb);
-        update_link_small<NT>(plane, V, s, sa, bu0 + (mu & 1) * 9 * NT, u, b);
+        if (mu < 3) fetch_b<NT>(A, V, site_fwd(L, s, mu + 1, c[mu + 1]), bb);
+        update_link_small<NT>(plane, V, s, sa, bu0, u, b);
+        if (mu < 3) fetch_u<NT>(plane + pstride, V, s, bu0);
       } else {
         update_link_general<NT>(plane, G, V, s, sf, bu);
-        if (mu < 3)
-          fetch_link<NT>(plane + pstride, A, V, s, site_fwd(L, s, mu + 1, c[mu + 1]), bu0 + ((mu + 1) & 1) * 9 * NT,
-                         bb);
+        if (mu < 3) fetch_link<NT>(plane + pstride, A, V, s, site_fwd(L, s, mu + 1, c[mu + 1]), bu0, bb);
       }
     }
   } else {
