@@ -5,11 +5,11 @@ roofline of the kernels.
 
 A step is one complete gauge fixing (Algorithm 1 of Cardoso et al., run until theta < 1e-15) of the
 64^4 configuration (eps = 0.6, seed 4; links 9.66 GB in double precision), with the mixed-precision
-schedule: float links, FFTs and updates with double reductions until theta <= 1e-8, then the double
+schedule: float links, FFTs and updates with double reductions until theta <= 1e-11, then the double
 handover and double precision to theta < 1e-15. The input stays resident in HBM and is never
 modified (load -> iterate -> store into a separate output buffer), so every step repeats the same
 work. `value` = V * iterations / time (site-iterations per second over whole fixes); `ms_per_step`
-is the time to theta < 1e-15. Beside it: the same field fixed in plain FP64, per-kernel device times
+is the time to theta < 1e-15. Beside it: the same field fixed in the double path, per-kernel device times
 from CUDA events recorded on the working stream during the timed steps, the end-to-end figure through
 the C ABI from pinned host buffers (copies included), and the CPU oracle timed on a bounded sample.
 
@@ -373,7 +373,7 @@ def main():
     ap.add_argument("--eps", type=float, default=0.6)
     ap.add_argument("--seed", type=int, default=4)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "fp32"])
-    ap.add_argument("--theta-switch", type=float, default=1e-8)
+    ap.add_argument("--theta-switch", type=float, default=1e-11)
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison fix")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

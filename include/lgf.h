@@ -53,7 +53,9 @@ typedef enum {
 
 typedef struct {
   int precision;       /* lgf_precision; default LGF_FP64                                          */
-  double theta_switch; /* LGF_MIXED: theta at which the float stage hands over; default 1e-8       */
+  double theta_switch; /* LGF_MIXED: theta at which the float stage hands over; default 1e-11. The
+                          float stage also hands over when a chunk of its iterations does not lower
+                          theta (the resolution of float links is reached)                          */
   int reunit_period;   /* float stages: links and accumulated transformation reprojected to SU(3)
                           in double precision every this many iterations; default 16               */
   int max_iter;        /* iteration limit; default 100000                                          */

@@ -159,7 +159,7 @@ class Lattice:
         self._check(_lib.lgf_set_stream(self._h, raw))
 
     @staticmethod
-    def options(precision="fp64", theta_switch=1e-8, reunit_period=16, max_iter=100000, history=None,
+    def options(precision="fp64", theta_switch=1e-11, reunit_period=16, max_iter=100000, history=None,
                 fft32_final=False):
         o = Options()
         _lib.lgf_default_options(ctypes.byref(o))
@@ -173,7 +173,7 @@ class Lattice:
             o.history_len = history.shape[0]
         return o
 
-    def fix(self, U, alpha=0.08, eps=1e-15, precision="fp64", max_iter=100000, theta_switch=1e-8,
+    def fix(self, U, alpha=0.08, eps=1e-15, precision="fp64", max_iter=100000, theta_switch=1e-11,
             reunit_period=16, history_len=0, fft32_final=False):
         """Algorithm 1: fix U in place. Returns dict(theta, F, iters, converged, history)."""
         hist = np.zeros((history_len, 2), dtype=np.float64) if history_len > 0 else None
@@ -198,7 +198,7 @@ class Lattice:
         self._bind(U)
         self._check(_lib.lgf_load(self._h, _ptr(U), _PREC[precision]))
 
-    def iterate(self, max_new, alpha=0.08, eps=1e-15, theta_switch=1e-8, reunit_period=16, history_len=0,
+    def iterate(self, max_new, alpha=0.08, eps=1e-15, theta_switch=1e-11, reunit_period=16, history_len=0,
                 fft32_final=False):
         hist = np.zeros((history_len, 2), dtype=np.float64) if history_len > 0 else None
         o = self.options("fp64", theta_switch, reunit_period, 0, hist, fft32_final)
@@ -291,7 +291,7 @@ class Batch:
     def __exit__(self, *a):
         self.close()
 
-    def fix(self, Us, alpha=0.08, eps=1e-15, precision="fp64", max_iter=100000, theta_switch=1e-8,
+    def fix(self, Us, alpha=0.08, eps=1e-15, precision="fp64", max_iter=100000, theta_switch=1e-11,
             reunit_period=16):
         """Fix every configuration of Us (list of links, device tensors or numpy arrays) in place.
         Returns a list of dict(theta, F, iters, status)."""

@@ -8,7 +8,7 @@
 // mixed schedule both the float-stage and the double-stage kernels, each running only for the
 // configurations in that stage -- are captured once in a CUDA graph and replayed until every
 // configuration has stopped; between replays the host hands over each mixed configuration that has
-// reached theta_switch. FFT pass shapes are chosen per (shape, precision) by a timing autotuner whose
+// reached theta_switch, or whose float stage did not lower theta over the last replay. FFT pass shapes are chosen per (shape, precision) by a timing autotuner whose
 // results are cached in a JSON file.
 
 // ------------------------------------------------------------------------------------------------
@@ -390,7 +390,10 @@ lgf_status lgf_batch_fix(lgf_batch *b, double *const *links, double alpha, doubl
     b->launches_per_replay = launches;
   }
   b->graph_replays = 0;
-  // replay until every configuration has stopped; hand over mixed configurations at theta_switch
+  // replay until every configuration has stopped; hand over mixed configurations at theta_switch, or
+  // when a replay of the float stage did not lower theta (the resolution of float links is reached)
+  std::vector<std::vector<std::pair<double, int>>> last(b->groups.size());
+  for (size_t k = 0; k < b->groups.size(); ++k) last[k].assign(b->groups[k]->nb, {0.0, -1});
   for (;;) {
     bool pending = false;
     for (size_t k = 0; k < b->groups.size(); ++k) {
@@ -403,9 +406,12 @@ lgf_status lgf_batch_fix(lgf_batch *b, double *const *links, double alpha, doubl
       for (int j = 0; j < g->nb; ++j) {
         Ctrl &c = host[k][j];
         if (c.status == 5) continue;
-        if (c.active) {
+        const bool stalled = prec == LGF_MIXED && c.stage == 0 && c.active && last[k][j].second >= 0 &&
+                             last[k][j].second < c.iters && !(c.theta < last[k][j].first);
+        last[k][j] = {c.theta, c.iters};
+        if (c.active && !stalled) {
           pending = true;
-        } else if (prec == LGF_MIXED && c.stage == 0 && c.theta < thr0 && c.iters < c.limit) {
+        } else if (prec == LGF_MIXED && c.stage == 0 && (c.theta < thr0 || stalled) && c.iters < c.limit) {
           BTRY(g, setup_precision<double>(g, g->s64));
           BTRY(g, handover_one(g, j));
           c.stage = 1;

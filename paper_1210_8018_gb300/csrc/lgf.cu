@@ -752,7 +752,7 @@ void lgf_default_options(lgf_options *opt) {
   if (!opt) return;
   opt->fft32_final = 0;
   opt->precision = LGF_FP64;
-  opt->theta_switch = 1e-8;
+  opt->theta_switch = 1e-11;
   opt->reunit_period = 16;
   opt->max_iter = 100000;
   opt->history = nullptr;
@@ -961,8 +961,11 @@ lgf_status lgf_iterate(lgf_ctx *ctx, int max_new, double alpha, double eps, cons
       result = LGF_ENONFINITE;
       break;
     }
-    if (c.theta < thr || c.iters >= target) {
-      if (mixed_float && c.theta < thr) {
+    // a float stage that no longer lowers theta over a chunk of iterations has reached what float links
+    // resolve: it hands over at once
+    const bool stalled = mixed_float && ctx->prev_theta > 0 && ctx->prev_iters < c.iters && !(c.theta < ctx->prev_theta);
+    if (c.theta < thr || c.iters >= target || stalled) {
+      if (mixed_float && (c.theta < thr || stalled)) {
         // hand over to double precision: rebuild the links from the input and G, then Delta, theta, F
         TRY(handover(ctx));
         ctx->stage = LGF_FP64;

@@ -52,7 +52,7 @@ def test_host_only_calls(lib):
     import paper_1210_8018_gb300 as lgf
     o = lgf.Options()
     lgf._lib.lgf_default_options(ctypes.byref(o))
-    assert o.precision == lgf.FP64 and o.theta_switch == 1e-8 and o.reunit_period == 16 and o.max_iter == 100000
+    assert o.precision == lgf.FP64 and o.theta_switch == 1e-11 and o.reunit_period == 16 and o.max_iter == 100000
     assert isinstance(lgf._lib.lgf_last_error(None), bytes)
 
 

@@ -67,3 +67,14 @@ def test_batch_limits_and_repeat(lgf):
         with lgf.Lattice(oracle.dims_of_links(U)) as lat:
             r1 = lat.fix(U.copy(), 0.08, 1e-15, "fp64")
         assert abs(r1["iters"] - r["iters"]) <= 1 and abs(r1["F"] - r["F"]) <= 1e-12 * abs(r1["F"])
+
+
+def test_batch_mixed_float_stage_hands_over_when_theta_stalls(lgf):
+    Us = configs()
+    work = [U.copy() for U in Us]
+    with lgf.Batch(SHAPES) as b:
+        res = b.fix(work, 0.08, 1e-15, "mixed", max_iter=1000, theta_switch=1e-30)
+    for U, Uf, r in zip(Us, work, res):
+        assert r["status"] == lgf.LGF_OK and r["theta"] < 1e-15 and r["iters"] < 1000
+        assert abs(oracle.plaquette(Uf) - oracle.plaquette(U)) < 1e-14
+        assert oracle.theta(oracle.delta(Uf)) < 1e-15

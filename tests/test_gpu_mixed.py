@@ -82,6 +82,23 @@ def test_mixed_store_mid_float_stage_is_gauge_equivalent(lgf):
     assert oracle.theta(oracle.delta(Us)) < 0.5 * th0
 
 
+def test_mixed_float_stage_hands_over_when_theta_stalls(lgf):
+    """A switch point below what float links resolve: the float stage stops lowering theta, hands over on
+    its own, and the double stage converges with the links still gauge-equivalent to the input."""
+    dims = (8, 8, 8, 8)
+    U = synth.config(dims, 1, 0.3)
+    with lgf.Lattice(dims) as lat:
+        r = lat.fix(U.copy(), 0.08, 1e-15, "mixed", max_iter=1000, theta_switch=1e-30)
+        Uf = U.copy()
+        r = lat.fix(Uf, 0.08, 1e-15, "mixed", max_iter=1000, theta_switch=1e-30)
+        r_ref = lat.fix(U.copy(), 0.08, 1e-15, "fp64")
+    assert r["converged"] and r["theta"] < 1e-15
+    assert r["iters"] < r_ref["iters"] + 40, (r, r_ref)
+    assert abs(r["F"] - r_ref["F"]) < 1e-12
+    assert abs(oracle.plaquette(Uf) - oracle.plaquette(U)) < 1e-14
+    assert oracle.theta(oracle.delta(Uf)) < 1e-15
+
+
 def test_fp32_precision_fix_reaches_float_floor(lgf):
     dims = (8, 8, 8, 8)
     U = synth.config(dims, 1, 0.3)
