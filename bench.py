@@ -41,9 +41,9 @@ UNIT = "site-iterations/s"
 FP64_FLOP_PER_CLK = 152 * 2 * 2      # 152 SMs x 2 DFMA per clock x 2 flop
 FP32_OPS_PER_CLK = 152 * 128         # 152 SMs x 128 FP32 lanes (one FADD, FMUL or FFMA each per clock)
 # DRAM bytes (read + write) per launch of a kernel at 64^4, from one ncu capture of
-# dram__bytes_read.sum + dram__bytes_write.sum (profiles/gauge_update_f64_64x4_traffic.md); valid only
-# for the kernel version that was captured.
-TRAFFIC_64 = {"gauge_update.f64": 14.54e9 + 10.12e9}
+# dram__bytes_read.sum + dram__bytes_write.sum (profiles/gauge_update_f64_64x4_traffic.md,
+# profiles/update_fused_f32_64x4_traffic.md); valid only for the kernel versions that were captured.
+TRAFFIC_64 = {"gauge_update.f64": 14.54e9 + 10.12e9, "gauge_update_fused.f32": 4.84e9 + 4.35e9}
 
 
 def peaks():
@@ -93,9 +93,9 @@ def work_model(kernel, dims):
         # schedule): rows 0-1 of g U (132 flop) and of (g U) g^+ (144), row 2 by a cross product (42).
         "gauge_update": ((4 * lp * 2 + 9) * es, 4 * 144 * 12 if prec == "f64" else 4 * LINK_PRODUCT_FLOP),
         # float stage: links read and written, G read and written (rows 0-1), packed Delta-tilde read (g is
-        # rebuilt in registers); the _reunit variant also projects the new links in double precision
+        # rebuilt in registers); the _reunit variant also projects G and the new links onto SU(3) in float
         "gauge_update_fused": ((4 * lp * 2 + 12 + 4) * es, 0),
-        "gauge_update_fused_reunit": ((4 * lp * 2 + 12 + 4) * es, 4 * PROJECTION_FLOP),
+        "gauge_update_fused_reunit": ((4 * lp * 2 + 12 + 4) * es, 0),
         "gacc_to_double": (6 * 8 + 9 * 16, PROJECTION_FLOP),
         "handover_transform": (36 * 16 * 2 + 9 * 16, 4 * LINK_PRODUCT_FLOP),
         "to_planes": (4 * lp * 16 + 4 * lp * es, 0),  # the float load reads rows 0-1 of each link only
@@ -115,7 +115,7 @@ def algorithmic(kernel, dims):
     if prec == "f64":
         kind = {"gauge_update": "fp32", "handover_transform": "fp64", "gacc_to_double": "fp64"}.get(name)
     else:
-        kind = "fp64" if name == "gauge_update_fused_reunit" else None
+        kind = None
     return b, (f if kind else 0), kind
 
 

@@ -57,7 +57,7 @@ typedef struct {
                           float stage also hands over when a chunk of its iterations does not lower
                           theta (the resolution of float links is reached)                          */
   int reunit_period;   /* float stages: links and accumulated transformation reprojected to SU(3)
-                          in double precision every this many iterations; default 16               */
+                          (in float) every this many iterations; default 16                        */
   int max_iter;        /* iteration limit; default 100000                                          */
   double *history;     /* optional host buffer: history[2k] = theta, history[2k+1] = F after k
                           updates (k = 0 is the input), for k < history_len                         */

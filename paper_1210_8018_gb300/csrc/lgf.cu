@@ -649,7 +649,7 @@ lgf_status launch_iteration_fft32(lgf_ctx *ctx, double alpha) {
 }
 
 // One iteration of the float stage (FP32 / mixed): g is rebuilt inside the update, which also
-// accumulates G and, every reunit_period iterations, reprojects the new links in double precision.
+// accumulates G and, every reunit_period iterations, reprojects G and the new links onto SU(3).
 lgf_status launch_iteration_float(lgf_ctx *ctx, double alpha, bool reunit) {
   State<float> &S = ctx->s32;
   TRY(launch_filter<float>(ctx, S, S.P, 1));

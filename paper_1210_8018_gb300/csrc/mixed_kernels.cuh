@@ -1,6 +1,6 @@
 // mixed_kernels.cuh -- kernels of the mixed-precision schedule: float links, FFTs and updates with the
 // accumulated gauge transformation G(x) = g_k(x) ... g_1(x) kept beside them, periodic reprojection of
-// the float links onto SU(3) in double precision, and the handover that rebuilds double
+// the float links and of G onto SU(3), and the handover that rebuilds double
 // links as G(x) U0_mu(x) G^+(x + mu) from the saved input U0, so that the double-precision stage
 // starts from links exactly gauge-equivalent to the input.
 #pragma once
@@ -19,8 +19,10 @@ __device__ __forceinline__ void gauge_from_packed(const float *P, int64_t V, int
 
 // Float-stage update with g rebuilt in registers: forms g(x) and the four g(x + mu) from the packed
 // Delta-tilde (no g field in memory), accumulates Gacc(x) <- g(x) Gacc(x) and applies
-// U_mu(x) -> g(x) U_mu(x) g^+(x + mu). With REUNIT the new links are projected onto SU(3) in double
-// precision before they are stored (the periodic reunitarisation of the float stage).
+// U_mu(x) -> g(x) U_mu(x) g^+(x + mu). With REUNIT the new G and the new links are projected onto SU(3)
+// before they are stored (the periodic reunitarisation of the float stage). The projection is done in
+// float: it only has to remove the drift from unitarity that float rounding accumulates between
+// projections, and the handover rebuilds double links from the saved input and a G projected in double.
 template <int NT, bool REUNIT>
 __global__ void __launch_bounds__(NT) k_update_fused_f32(float *__restrict__ U, const float *__restrict__ P,
                                                         float *__restrict__ Gacc, float half_alpha, Lattice L,
@@ -46,6 +48,7 @@ __global__ void __launch_bounds__(NT) k_update_fused_f32(float *__restrict__ U, 
   for (int e = 0; e < 6; ++e) a.e[e] = ld(Gacc, (int64_t)e * V + s);
   complete_row2(a);
   mul_rows01(gx, a, t);
+  if constexpr (REUNIT) reunitarize(t);
 #pragma unroll
   for (int e = 0; e < 6; ++e) st(Gacc, (int64_t)e * V + s, t.e[e]);
 #pragma unroll 1
@@ -57,16 +60,7 @@ __global__ void __launch_bounds__(NT) k_update_fused_f32(float *__restrict__ U, 
     gauge_from_packed(P, V, sf, half_alpha, gy);
     mul_rows01(gx, u, t);
     mul_adj_rows01(t, gy, u);
-    if constexpr (REUNIT) {
-      // (float <-> double by integer operations: the conversion instructions would share the FP64 pipe
-      // with the projection)
-      m3<double> d;
-#pragma unroll
-      for (int e = 0; e < 6; ++e) d.e[e] = {widen_bits(u.e[e].r), widen_bits(u.e[e].i)};
-      reunitarize(d);
-#pragma unroll
-      for (int e = 0; e < 6; ++e) u.e[e] = {narrow_bits(d.e[e].r), narrow_bits(d.e[e].i)};
-    }
+    if constexpr (REUNIT) reunitarize(u);
     store_link(plane, V, s, u);
   }
 }
