@@ -54,6 +54,10 @@ enum KernelId {
   KID_TO_PLANES,
   KID_FROM_PLANES,
   KID_SET_IDENTITY,
+  KID_DELTA_RESIDUAL,
+  KID_UPDATE_RESIDUAL,
+  KID_COMPOSE_RESIDUAL,
+  KID_RESIDUAL_BASE,
   KID_COUNT
 };
 // kernel names; the float instance of a kernel is reported with the suffix .f32, the double with .f64
@@ -62,7 +66,8 @@ const char *kKernelBase[KID_COUNT] = {"delta_theta",   "fft_xy_fwd",    "fft_x_f
                                       "fft_y_inv",     "fft_x_inv",     "fft_xy_inv",     "gauge_g",
                                       "gauge_update",  "gauge_update_fused", "gauge_update_fused_reunit",
                                       "gacc_to_double", "handover_transform", "to_planes", "from_planes",
-                                      "set_identity"};
+                                      "set_identity",  "delta_residual", "update_residual", "compose_residual",
+                                      "residual_base"};
 std::string kKernelNames[2 * KID_COUNT];
 template <typename T> int kid(int k) { return std::is_same<T, float>::value ? k + KID_COUNT : k; }
 
@@ -112,6 +117,8 @@ struct lgf_ctx {
   double *lam = nullptr;    // and its eigenvalues (3 planes of doubles)
   double *U0 = nullptr;     // mixed: input links (double planes) for the handover
   float *Gacc = nullptr;    // mixed/float: accumulated gauge transformation (9 float planes)
+  float *Rres = nullptr;    // mixed, residual stage: link residual R (4 x 9 float planes)
+  float *Kres = nullptr;    // and K = H - 1 (9 float planes)
   double *staging = nullptr;  // AoS double buffer for host inputs / outputs and single steps
   size_t staging_bytes = 0;
   double *staging2 = nullptr;
@@ -131,6 +138,9 @@ struct lgf_ctx {
   int since_reunit = 0;
   bool generic_fft = false;  // force the generic FFT passes (tests compare the two families)
   bool fft_df64 = true;      // double state: Fourier filter in df64 (LGF_FFT_NATIVE_F64=1: IEEE double)
+  bool residual = true;      // mixed: residual stage after the handover (LGF_RESIDUAL=0: double iterations)
+  bool resid_off = false;    // this load: a rebuild made no progress, the double stage continues
+  double resid_F = 0, resid_theta0 = 0;  // F and theta of the residual stage's base links
   bool small_step = true;    // double g and update: small-step forms where they apply (LGF_SMALL_STEP=0: never)
   int fixed_cols[2] = {0, 0};  // column width of the specialised passes (double, float); 0 = default
   double prev_theta = 0;  // theta and iteration count at the previous chunk boundary
@@ -695,6 +705,80 @@ lgf_status handover(lgf_ctx *ctx) {
   return timed_end(ctx);
 }
 
+// Residual stage of the mixed schedule (mixed_kernels.cuh), stage code kHostStageResidual on the host and
+// kStageResidual in the loop control. Entered from the double state: s64.U holds the base links U_h,
+// s64.P their packed Delta, s64.G the transformation G with U_h = G U0 G^+, and the loop control their
+// theta and F.
+constexpr int kHostStageResidual = 3;
+
+lgf_status launch_delta_residual(lgf_ctx *ctx, int counts_update) {
+  TRY(timed_begin(ctx, kid<float>(KID_DELTA_RESIDUAL)));
+  TRY(with_fft_type<double>(ctx, [&](auto tag) -> lgf_status {
+    using FT = decltype(tag);
+    k_delta_residual<NT, FT><<<ctx->nblocks_site, NT, 0, ctx->stream>>>(
+        ctx->Rres, reinterpret_cast<const FT *>(ctx->s64.P), ctx->s32.P, ctx->partials, ctx->ctrl, ctx->L,
+        ctx->resid_F, counts_update, kid<float>(KID_DELTA_RESIDUAL));
+    CKL();
+    return LGF_OK;
+  }));
+  return timed_end(ctx);
+}
+
+lgf_status residual_begin(lgf_ctx *ctx) {
+  const int64_t V = ctx->V;
+  TRY(setup_precision<float>(ctx, ctx->s32));
+  TRY(alloc(ctx, &ctx->Rres, (size_t)36 * V * 2));
+  TRY(alloc(ctx, &ctx->Kres, (size_t)9 * V * 2));
+  TRY(timed_begin(ctx, kid<float>(KID_RESIDUAL_BASE)));
+  k_narrow_link_planes<<<grid1((int64_t)4 * V, NT), NT, 0, ctx->stream>>>(ctx->s64.U, ctx->s32.U, V);
+  CKL();
+  TRY(timed_end(ctx));
+  CK(cudaMemsetAsync(ctx->Rres, 0, sizeof(float) * 72 * (size_t)V, ctx->stream));
+  CK(cudaMemsetAsync(ctx->Kres, 0, sizeof(float) * 18 * (size_t)V, ctx->stream));
+  Ctrl &c = ctx->ctrl_host;
+  ctx->resid_F = c.F;
+  ctx->resid_theta0 = c.theta;
+  ctx->stage = kHostStageResidual;
+  ctx->prev_theta = 0;
+  c.stage = kStageResidual;
+  c.active = 1;
+  TRY(write_ctrl(ctx));
+  TRY(launch_delta_residual(ctx, 0));  // Delta = Delta(U_h) packed in float, and theta, F
+  return read_ctrl(ctx);
+}
+
+lgf_status launch_iteration_residual(lgf_ctx *ctx, double alpha) {
+  TRY(launch_filter<float>(ctx, ctx->s32, ctx->s32.P, 2));
+  TRY(timed_begin(ctx, kid<float>(KID_UPDATE_RESIDUAL)));
+  k_update_residual<NT><<<grid1(ctx->V, NT), NT, 0, ctx->stream>>>(ctx->s32.U, ctx->Rres, ctx->Kres, ctx->s32.P,
+                                                                 (float)(0.5 * alpha), ctx->L, ctx->ctrl,
+                                                                 kid<float>(KID_UPDATE_RESIDUAL));
+  CKL();
+  TRY(timed_end(ctx));
+  return launch_delta_residual(ctx, 1);
+}
+
+// End of the residual stage: G <- proj(1 + K) G, links rebuilt from the saved input in double, and
+// Delta, theta and F of the rebuilt links in double. Leaves the double state.
+lgf_status residual_rebuild(lgf_ctx *ctx) {
+  TRY(timed_begin(ctx, kid<double>(KID_COMPOSE_RESIDUAL)));
+  k_compose_residual<NT><<<grid1(ctx->V, NT), NT, 0, ctx->stream>>>(ctx->Kres, ctx->s64.G, ctx->V);
+  CKL();
+  TRY(timed_end(ctx));
+  TRY(timed_begin(ctx, kid<double>(KID_TRANSFORM_FROM)));
+  k_transform_from<NT><<<grid1(ctx->V, NT), NT, 0, ctx->stream>>>(ctx->U0, ctx->s64.U, ctx->s64.G, ctx->L);
+  CKL();
+  TRY(timed_end(ctx));
+  Ctrl &c = ctx->ctrl_host;
+  ctx->stage = LGF_FP64;
+  ctx->prev_theta = 0;
+  c.stage = 1;
+  c.active = 1;
+  TRY(write_ctrl(ctx));
+  TRY(launch_delta<double>(ctx, ctx->s64, 0, 0));
+  return read_ctrl(ctx);
+}
+
 // Timed wrappers of the layout conversions used by load and store.
 // nmat = 4: links (stored with LinkStore<T>::planes planes); nmat = 1: a site field of 9 planes.
 template <typename T> lgf_status to_planes(lgf_ctx *ctx, const double *src, T *dst, int nmat) {
@@ -806,6 +890,8 @@ static lgf_status create_ctx(const int n[4], int nb, lgf_ctx **out) {
     ctx->fft_df64 = !(nf && nf[0] == '1');
     const char *ss = std::getenv("LGF_SMALL_STEP");
     ctx->small_step = !(ss && ss[0] == '0');
+    const char *rs = std::getenv("LGF_RESIDUAL");
+    ctx->residual = !(rs && rs[0] == '0');
   }
   cudaDeviceGetAttribute(&ctx->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
   // p^2 tables (position -> 4 sin^2(pi k / N)) and the filter scale p^2_max / V
@@ -858,6 +944,8 @@ void lgf_destroy(lgf_ctx *ctx) {
   fr(ctx->Wev);
   fr(ctx->lam);
   fr(ctx->Gacc);
+  fr(ctx->Rres);
+  fr(ctx->Kres);
   fr(ctx->staging);
   fr(ctx->staging2);
   fr(ctx->partials);
@@ -931,6 +1019,7 @@ lgf_status lgf_load(lgf_ctx *ctx, const double *links, int precision) {
   ctx->since_reunit = 0;
   ctx->prev_theta = 0;
   ctx->prev_iters = 0;
+  ctx->resid_off = false;
   return LGF_OK;
 }
 
@@ -955,20 +1044,38 @@ lgf_status lgf_iterate(lgf_ctx *ctx, int max_new, double alpha, double eps, cons
   for (;;) {
     const bool float_stage = ctx->stage == LGF_FP32;
     const bool mixed_float = float_stage && ctx->load_prec == LGF_MIXED;
-    const double thr = mixed_float ? std::max(eps, o.theta_switch) : eps;
+    const bool resid_stage = ctx->stage == kHostStageResidual;
+    // the residual stage stops a little below eps: its float theta is checked again in double after
+    // the rebuild
+    const double thr = mixed_float ? std::max(eps, o.theta_switch) : resid_stage ? 0.8 * eps : eps;
     Ctrl &c = ctx->ctrl_host;
     if (c.status == 5) {
       result = LGF_ENONFINITE;
       break;
     }
-    // a float stage that no longer lowers theta over a chunk of iterations has reached what float links
-    // resolve: it hands over at once
-    const bool stalled = mixed_float && ctx->prev_theta > 0 && ctx->prev_iters < c.iters && !(c.theta < ctx->prev_theta);
+    // the mixed schedule past the handover continues in the residual stage while theta >= eps
+    if (ctx->stage == LGF_FP64 && ctx->load_prec == LGF_MIXED && ctx->residual && !o.fft32_final &&
+        !ctx->resid_off && !(c.theta < eps) && c.iters < target) {
+      TRY(residual_begin(ctx));
+      continue;
+    }
+    // a float or residual stage that no longer lowers theta over a chunk of iterations has reached what
+    // its float arithmetic resolves: it hands over (or rebuilds) at once
+    const bool stalled = (mixed_float || resid_stage) && ctx->prev_theta > 0 && ctx->prev_iters < c.iters &&
+                         !(c.theta < ctx->prev_theta);
     if (c.theta < thr || c.iters >= target || stalled) {
+      if (resid_stage) {
+        // rebuild the double links; without progress over the stage the double iterations take over
+        const double theta0 = ctx->resid_theta0;
+        TRY(residual_rebuild(ctx));
+        if (!(ctx->ctrl_host.theta < theta0)) ctx->resid_off = true;
+        continue;
+      }
       if (mixed_float && (c.theta < thr || stalled)) {
         // hand over to double precision: rebuild the links from the input and G, then Delta, theta, F
         TRY(handover(ctx));
         ctx->stage = LGF_FP64;
+        ctx->prev_theta = 0;
         c.active = 1;
         c.stage = 1;
         TRY(write_ctrl(ctx));
@@ -995,7 +1102,9 @@ lgf_status lgf_iterate(lgf_ctx *ctx, int max_new, double alpha, double eps, cons
     ctx->prev_theta = c.theta;
     ctx->prev_iters = c.iters;
     for (int k = 0; k < chunk; ++k) {
-      if (float_stage) {
+      if (resid_stage) {
+        TRY(launch_iteration_residual(ctx, alpha));
+      } else if (float_stage) {
         const bool reunit = ++ctx->since_reunit >= o.reunit_period;
         if (reunit) ctx->since_reunit = 0;
         TRY(launch_iteration_float(ctx, alpha, reunit));
@@ -1027,6 +1136,7 @@ lgf_status lgf_store(lgf_ctx *ctx, double *links) {
   double *dst = nullptr;
   bool host = false;
   TRY(output_ptr(ctx, links, bytes, &ctx->staging, &ctx->staging_bytes, &dst, &host));
+  if (ctx->stage == kHostStageResidual) TRY(residual_rebuild(ctx));
   if (ctx->stage == LGF_FP64) {
     TRY(from_planes<double>(ctx, ctx->s64.U, dst, 4));
   } else if (ctx->load_prec == LGF_MIXED) {
@@ -1343,7 +1453,8 @@ lgf_status lgf_kernel_times(lgf_ctx *ctx, const char **name, long *launches, dou
     CK(cudaMemset(ctx->ran_dev, 0, sizeof ran));
     const int loop_kids[] = {KID_DELTA, KID_FFT_XY_FWD, KID_FFT_X_FWD, KID_FFT_Y_FWD, KID_FFT_Z_FWD,
                              KID_FFT_ZT_FILTER, KID_FFT_T_FILTER, KID_FFT_Z_INV, KID_FFT_Y_INV, KID_FFT_X_INV,
-                             KID_FFT_XY_INV, KID_GAUGE, KID_UPDATE, KID_UPDATE_FUSED, KID_UPDATE_FUSED_REUNIT};
+                             KID_FFT_XY_INV, KID_GAUGE, KID_UPDATE, KID_UPDATE_FUSED, KID_UPDATE_FUSED_REUNIT,
+                             KID_DELTA_RESIDUAL, KID_UPDATE_RESIDUAL};
     for (int k : loop_kids)
       for (int h = 0; h < 2; ++h) {
         const int i = k + h * KID_COUNT;

@@ -133,4 +133,163 @@ __global__ void k_set_identity(float *__restrict__ Gacc, int64_t V) {
   for (int e = 0; e < 6; ++e) st(Gacc, (int64_t)e * V + s, mkc((e % 4 == 0) ? 1.0f : 0.0f, 0.0f));  // rows 0-1
 }
 
+// ---------------------------------------------------------------------------------------------
+// Residual stage of the mixed schedule (after the handover). The links are U = U_h + R: U_h are the
+// handover links (double, fixed for the stage) and R, a float residual starting at zero, takes every
+// change. Delta is linear in the links, so Delta(U) = Delta(U_h) + Delta(R) with Delta(U_h) computed
+// once in double. The update needs U only to float accuracy (it multiplies the small a and b), and
+// reads it as B + R with B = U_h rounded to float (rows 0-1, the float link planes). Every float
+// quantity of the stage (a = g - 1, R, K with H = 1 + K the transformation gathered in the stage) is of
+// the size of the remaining gauge transformation, so its rounding is relative to that size and not to
+// the O(1) links: with changes of order 1e-4 the links are tracked to about 1e-11 and Delta to about
+// 1e-10, against entries of 3e-8 at theta = 1e-15. The stage ends with G <- proj(H) G in double and the
+// links rebuilt from the saved input in double (k_transform_from), so the result is exactly
+// gauge-equivalent to the input; theta is then recomputed in double.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ bool residual_active(const Ctrl *ctrl) {
+  return ctrl->active && ctrl->stage == kStageResidual;
+}
+
+__device__ __forceinline__ float packed_to_float(df64 v) { return __fadd_rn(v.hi, v.lo); }
+__device__ __forceinline__ float packed_to_float(double v) { return narrow_bits(v); }
+
+template <typename T> __device__ __forceinline__ void load9(const T *plane, int64_t V, int64_t s, m3<T> &u) {
+#pragma unroll
+  for (int e = 0; e < 9; ++e) u.e[e] = ldg(plane, (int64_t)e * V + s);
+}
+
+// Delta = Delta(U_h) + Delta(R) (packed, float), theta and F = F_h + sum Re Tr R / (12 V) (a1/a2).
+// Ph: packed Delta(U_h) in the double state's FFT type PT.
+template <int NT, typename PT>
+__global__ void __launch_bounds__(NT) k_delta_residual(const float *__restrict__ R, const PT *__restrict__ Ph,
+                                                      float *__restrict__ P, double *partials, Ctrl *ctrl, Lattice L,
+                                                      double F_h, int counts_update, int tkid) {
+  const int64_t V = L.V;
+  if (!residual_active(ctrl)) return;
+  count_run(ctrl, tkid);
+  double th = 0.0, f = 0.0;
+#pragma unroll 1
+  for (int k = 0; k < kSitesPerThread; ++k) {
+    const int64_t s = ((int64_t)blockIdx.x * kSitesPerThread + k) * NT + threadIdx.x;
+    if (s >= V) break;
+    int c[4];
+    site_coords(L, s, c);
+    float acc[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) acc[e] = 0.f;
+    float fs = 0.f;
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      const float *plane = R + (int64_t)mu * 18 * V;
+      m3<float> u;
+      load9(plane, V, site_back(L, s, mu, c[mu]), u);  // R_mu(x - mu)
+      accumulate_link(u, 1.f, acc);
+      load9(plane, V, s, u);  // - R_mu(x)
+      accumulate_link(u, -1.f, acc);
+      fs += u.e[0].r + u.e[4].r + u.e[8].r;
+    }
+    const float m = (acc[6] + acc[7] + acc[8]) / 3.f;
+    float d[8] = {acc[0], acc[1], acc[2], acc[3], acc[4], acc[5], 2.f * (acc[6] - m), 2.f * (acc[7] - m)};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const cx<PT> h = ldg(Ph, (int64_t)q * V + s);
+      d[2 * q] += packed_to_float(h.r);
+      d[2 * q + 1] += packed_to_float(h.i);
+    }
+    const float a2 = -(d[6] + d[7]);
+    const float ts = d[6] * d[6] + d[7] * d[7] + a2 * a2 +
+                     2.f * (d[0] * d[0] + d[1] * d[1] + d[2] * d[2] + d[3] * d[3] + d[4] * d[4] + d[5] * d[5]);
+    th += widen_bits(ts);
+    f += widen_bits(fs);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) st(P, (int64_t)q * V + s, mkc(d[2 * q], d[2 * q + 1]));
+  }
+  reduce_and_finalize<NT>(th, f, partials, ctrl, V, counts_update, F_h);
+}
+
+// a = g - 1 with g the SU(3) projection of 1 + X, in float: the small-step form when every |X| < 2^-8,
+// else Gram-Schmidt of 1 + X minus the identity (large steps, where float rounding of a is harmless).
+__device__ __forceinline__ void residual_step(const m3<float> &X, m3<float> &a) {
+  float mx = 0.f;
+#pragma unroll
+  for (int e = 0; e < 9; ++e) mx = fmaxf(mx, fmaxf(fabsf(X.e[e].r), fabsf(X.e[e].i)));
+  if (mx < 0x1p-8f) {
+    small_step_projection(X, a);
+    return;
+  }
+  a = X;
+  a.e[0].r += 1.f;
+  a.e[4].r += 1.f;
+  a.e[8].r += 1.f;
+  reunitarize(a);
+  a.e[0].r -= 1.f;
+  a.e[4].r -= 1.f;
+  a.e[8].r -= 1.f;
+}
+
+// a6 + a7 on the residual: a(x) and b = g(x + mu) - 1 from the packed Delta-tilde (float), K <- a + K + a K
+// (H <- g H), and R_mu(x) <- R_mu(x) + a U + (U + a U) b^+ with U = B + R (U -> g U g^+(x + mu)).
+// B: float link planes (rows 0-1; row 2 completed on load).
+template <int NT>
+__global__ void __launch_bounds__(NT) k_update_residual(const float *__restrict__ B, float *__restrict__ R,
+                                                       float *__restrict__ K, const float *__restrict__ P,
+                                                       float half_alpha, Lattice L, const Ctrl *ctrl, int tkid) {
+  const int64_t V = L.V;
+  if (!residual_active(ctrl)) return;
+  count_run(ctrl, tkid);
+  const int64_t s = (int64_t)blockIdx.x * NT + threadIdx.x;
+  if (s >= V) return;
+  int c[4];
+  site_coords(L, s, c);
+  m3<float> X, a, t;
+  unpack_scaled(P, V, s, half_alpha, X);
+  residual_step(X, a);
+  {
+    m3<float> k;
+    load9(K, V, s, k);
+    mul(a, k, t);
+#pragma unroll
+    for (int e = 0; e < 9; ++e) st(K, (int64_t)e * V + s, (a.e[e] + k.e[e]) + t.e[e]);
+  }
+#pragma unroll 1
+  for (int mu = 0; mu < 4; ++mu) {
+    m3<float> b, u, r, w;
+    unpack_scaled(P, V, site_fwd(L, s, mu, c[mu]), half_alpha, X);
+    residual_step(X, b);
+    float *rp = R + (int64_t)mu * 18 * V;
+    load9(rp, V, s, r);
+    load_link(B + (int64_t)mu * link_plane_stride<float>(V), V, s, u);
+#pragma unroll
+    for (int e = 0; e < 9; ++e) u.e[e] = u.e[e] + r.e[e];
+    mul(a, u, t);  // a U
+#pragma unroll
+    for (int e = 0; e < 9; ++e) w.e[e] = u.e[e] + t.e[e];  // g U
+    mul_adj(w, b, u);                                      // (g U) b^+
+#pragma unroll
+    for (int e = 0; e < 9; ++e) st(rp, (int64_t)e * V + s, r.e[e] + (t.e[e] + u.e[e]));
+  }
+}
+
+// G <- proj(1 + K) G in double: H projected onto SU(3) by Gram-Schmidt in FP64, then the product.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_compose_residual(const float *__restrict__ K, double *__restrict__ G,
+                                                        int64_t V) {
+  const int64_t s = (int64_t)blockIdx.x * NT + threadIdx.x;
+  if (s >= V) return;
+  m3<double> h, g, t;
+#pragma unroll
+  for (int e = 0; e < 9; ++e) {
+    const cx<float> k = ldg(K, (int64_t)e * V + s);
+    h.e[e] = {widen_bits(k.r), widen_bits(k.i)};
+  }
+  h.e[0].r += 1.0;
+  h.e[4].r += 1.0;
+  h.e[8].r += 1.0;
+  reunitarize(h);
+  load9(G, V, s, g);
+  mul(h, g, t);
+#pragma unroll
+  for (int e = 0; e < 9; ++e) st(G, (int64_t)e * V + s, t.e[e]);
+}
+
 }  // namespace lgf

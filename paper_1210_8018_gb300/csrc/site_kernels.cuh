@@ -38,9 +38,11 @@ struct Ctrl {
   int hist_len;
   double *hist;          // device history: hist[2k], hist[2k+1] = theta, F after k updates
   unsigned int *ran;     // optional per-kernel counters of launches that did work (timing mode)
-  int stage;             // precision of the live links: 0 float, 1 double; kernels of the other
-                         // precision return at once (a batch launches both in the mixed schedule)
+  int stage;             // precision of the live links: 0 float, 1 double, 2 the residual stage of the
+                         // mixed schedule; kernels of another stage return at once (a batch launches
+                         // the float and the double kernels in the mixed schedule)
 };
+constexpr int kStageResidual = 2;
 
 // Count a launch that does work (block 0, thread 0), for the per-kernel timing statistics.
 __device__ __forceinline__ void count_run(const Ctrl *ctrl, int tkid) {
@@ -127,10 +129,10 @@ template <int NT> __device__ __forceinline__ void block_sum2(double &a, double &
 
 // Writes this block's (sum_theta, sum_F) partial; the last block to arrive reduces all partials in a
 // fixed order and updates the loop control (Algorithm 1: "calculate Delta(x), F and theta", then the
-// while-test theta >= eps).
+// while-test theta >= eps). f_offset is added to F (the residual stage sums only the residual's traces).
 template <int NT>
 __device__ __forceinline__ void reduce_and_finalize(double th, double f, double *partials, Ctrl *ctrl, int64_t V,
-                                                    int counts_update) {
+                                                    int counts_update, double f_offset = 0.0) {
   __shared__ bool last;
   block_sum2<NT>(th, f);
   if (threadIdx.x == 0) {
@@ -152,7 +154,7 @@ __device__ __forceinline__ void reduce_and_finalize(double th, double f, double 
   block_sum2<NT>(a, b);
   if (threadIdx.x == 0) {
     const double theta = a / (3.0 * (double)V);  // Eq. 4: 1/(N_c V) sum_x Tr[Delta Delta^+]
-    const double F = b / (12.0 * (double)V);     // Eq. 1 at g = 1: 1/(4 N_c V) sum Re Tr U
+    const double F = b / (12.0 * (double)V) + f_offset;  // Eq. 1 at g = 1: 1/(4 N_c V) sum Re Tr U
     ctrl->ticket = 0;
     int it = ctrl->iters + counts_update;
     ctrl->iters = it;
@@ -360,27 +362,28 @@ __device__ __forceinline__ void unpack_scaled(const PT *P, int64_t V, int64_t s,
 constexpr int kSmallXFloatExpField = 127 - 9;  // |x| < 2^-8  <=>  float exponent field <= 118
 
 __device__ __forceinline__ int fexp_field(float x) { return (int)((__float_as_uint(x) >> 23) & 0xFF); }
-__device__ __forceinline__ df64 rsqrt1p_m1(df64 t) {
-  return t * (kconst<df64>(-0.5) + t * (kconst<df64>(0.375) + t * kconst<df64>(-0.3125)));
+template <typename T> __device__ __forceinline__ T rsqrt1p_m1(T t) {
+  return t * (kconst<T>(-0.5) + t * (kconst<T>(0.375) + t * kconst<T>(-0.3125)));
 }
-__device__ __forceinline__ void small_step_projection(const m3<df64> &X, m3<df64> &a) {
-  const df64 one = kconst<df64>(1.0);
-  const df64 t0 = kconst<df64>(2.0) * X.e[0].r + (norm2(X.e[0]) + norm2(X.e[1]) + norm2(X.e[2]));
-  const df64 c0 = rsqrt1p_m1(t0), s0 = one + c0;
-  a.e[0] = scale(X.e[0], s0) + cx<df64>{c0, kconst<df64>(0.0)};
+// (T = df64 for the double path; T = float for the residual stage of the mixed schedule)
+template <typename T> __device__ __forceinline__ void small_step_projection(const m3<T> &X, m3<T> &a) {
+  const T one = kconst<T>(1.0);
+  const T t0 = kconst<T>(2.0) * X.e[0].r + (norm2(X.e[0]) + norm2(X.e[1]) + norm2(X.e[2]));
+  const T c0 = rsqrt1p_m1(t0), s0 = one + c0;
+  a.e[0] = scale(X.e[0], s0) + cx<T>{c0, kconst<T>(0.0)};
   a.e[1] = scale(X.e[1], s0);
   a.e[2] = scale(X.e[2], s0);
-  cx<df64> p = conjg(a.e[1]) + X.e[3];
+  cx<T> p = conjg(a.e[1]) + X.e[3];
 #pragma unroll
   for (int j = 0; j < 3; ++j) p = p + conjg(a.e[j]) * X.e[3 + j];
-  cx<df64> d[3];
+  cx<T> d[3];
   d[0] = X.e[3] - p - p * a.e[0];
   d[1] = X.e[4] - p * a.e[1];
   d[2] = X.e[5] - p * a.e[2];
-  const df64 t1 = kconst<df64>(2.0) * d[1].r + (norm2(d[0]) + norm2(d[1]) + norm2(d[2]));
-  const df64 c1 = rsqrt1p_m1(t1), s1 = one + c1;
+  const T t1 = kconst<T>(2.0) * d[1].r + (norm2(d[0]) + norm2(d[1]) + norm2(d[2]));
+  const T c1 = rsqrt1p_m1(t1), s1 = one + c1;
   a.e[3] = scale(d[0], s1);
-  a.e[4] = scale(d[1], s1) + cx<df64>{c1, kconst<df64>(0.0)};
+  a.e[4] = scale(d[1], s1) + cx<T>{c1, kconst<T>(0.0)};
   a.e[5] = scale(d[2], s1);
   a.e[6] = conjg(a.e[1] * a.e[5] - a.e[2] * a.e[4] - a.e[2]);
   a.e[7] = conjg(a.e[2] * a.e[3] - a.e[0] * a.e[5] - a.e[5]);
