@@ -97,18 +97,20 @@ def work_model(kernel, dims):
         "gauge_update_fused": ((4 * lp * 2 + 12 + 4) * es, 0),
         "gauge_update_fused_reunit": ((4 * lp * 2 + 12 + 4) * es, 0),
         "gacc_to_double": (6 * 8 + 9 * 16, PROJECTION_FLOP),
-        "handover_transform": (36 * 16 * 2 + 9 * 16, 4 * LINK_PRODUCT_FLOP),
+        "handover_transform": (36 * 16 * 2 + 9 * 16 + 4 * 6 * 8, 4 * LINK_PRODUCT_FLOP),
         "to_planes": (4 * lp * 16 + 4 * lp * es, 0),  # the float load reads rows 0-1 of each link only
         "from_planes": (4 * lp * es + 36 * 16, 0),
         "set_identity": (6 * 8, 0),
         # residual stage of the mixed schedule: Delta from the residual R (4 x 9 float planes read) plus the
         # base's packed Delta (4 x 16 B) into the float packed field; the update reads the base links (rows
         # 0-1, float), reads and writes R and K = H - 1 (9 float planes) and reads the packed Delta-tilde;
-        # the compose step reads K and reads and writes G (double), with one FP64 projection and one 3 x 3
-        # complex product (9 x 22 flop); the base is the double links narrowed to float rows 0-1.
+        # at the end H is projected in FP64 (K read, H and a = H - 1 written) and the double links are
+        # rebuilt by the double update (the same counts as gauge_update.f64); the base (only when the stage
+        # restarts from rebuilt links) is the double links narrowed to float rows 0-1.
         "delta_residual": (4 * 9 * 8 + 4 * 16 + 4 * 8, 0),
         "update_residual": (4 * 6 * 8 + 2 * 4 * 9 * 8 + 2 * 9 * 8 + 4 * 8, 0),
-        "compose_residual": (9 * 8 + 2 * 9 * 16, PROJECTION_FLOP + 9 * 22),
+        "residual_gauge": (9 * 8 + 9 * 16 + 9 * 16, PROJECTION_FLOP),
+        "residual_rebuild": ((4 * 9 * 2 + 9) * 16, 4 * 144 * 12),
         "residual_base": (4 * 6 * 16 + 4 * 6 * 8, 0),
     }
     b, f = table[name]
@@ -122,8 +124,8 @@ def algorithmic(kernel, dims):
     b, f, prec = work_model(kernel, dims)
     name = kernel.rsplit(".", 1)[0]
     if prec == "f64":
-        kind = {"gauge_update": "fp32", "handover_transform": "fp64", "gacc_to_double": "fp64",
-                "compose_residual": "fp64"}.get(name)
+        kind = {"gauge_update": "fp32", "residual_rebuild": "fp32", "handover_transform": "fp64",
+                "gacc_to_double": "fp64", "residual_gauge": "fp64"}.get(name)
     else:
         kind = None
     return b, (f if kind else 0), kind

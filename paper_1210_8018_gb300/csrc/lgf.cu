@@ -56,7 +56,8 @@ enum KernelId {
   KID_SET_IDENTITY,
   KID_DELTA_RESIDUAL,
   KID_UPDATE_RESIDUAL,
-  KID_COMPOSE_RESIDUAL,
+  KID_RESIDUAL_GAUGE,
+  KID_RESIDUAL_REBUILD,
   KID_RESIDUAL_BASE,
   KID_COUNT
 };
@@ -66,8 +67,8 @@ const char *kKernelBase[KID_COUNT] = {"delta_theta",   "fft_xy_fwd",    "fft_x_f
                                       "fft_y_inv",     "fft_x_inv",     "fft_xy_inv",     "gauge_g",
                                       "gauge_update",  "gauge_update_fused", "gauge_update_fused_reunit",
                                       "gacc_to_double", "handover_transform", "to_planes", "from_planes",
-                                      "set_identity",  "delta_residual", "update_residual", "compose_residual",
-                                      "residual_base"};
+                                      "set_identity",  "delta_residual", "update_residual", "residual_gauge",
+                                      "residual_rebuild", "residual_base"};
 std::string kKernelNames[2 * KID_COUNT];
 template <typename T> int kid(int k) { return std::is_same<T, float>::value ? k + KID_COUNT : k; }
 
@@ -140,6 +141,7 @@ struct lgf_ctx {
   bool fft_df64 = true;      // double state: Fourier filter in df64 (LGF_FFT_NATIVE_F64=1: IEEE double)
   bool residual = true;      // mixed: residual stage after the handover (LGF_RESIDUAL=0: double iterations)
   bool resid_off = false;    // this load: a rebuild made no progress, the double stage continues
+  bool resid_base_ready = false;  // the float link planes hold the double links rounded (by the handover)
   double resid_F = 0, resid_theta0 = 0;  // F and theta of the residual stage's base links
   bool small_step = true;    // double g and update: small-step forms where they apply (LGF_SMALL_STEP=0: never)
   int fixed_cols[2] = {0, 0};  // column width of the specialised passes (double, float); 0 = default
@@ -692,16 +694,20 @@ lgf_status write_ctrl(lgf_ctx *ctx) {
 }
 
 // Mixed handover: G from the float accumulation (reprojected in double), then
-// U = G U0 G^+(x+mu) in double precision from the saved input (exact gauge equivalence).
-lgf_status handover(lgf_ctx *ctx) {
+// U = G U0 G^+(x+mu) in double precision from the saved input (exact gauge equivalence). With
+// write_base, rows 0-1 of U rounded to float also go to the float link planes (the residual stage's
+// base; the float stage's links are not needed after the handover).
+lgf_status handover(lgf_ctx *ctx, bool write_base = false) {
   TRY(setup_precision<double>(ctx, ctx->s64));
   TRY(timed_begin(ctx, kid<double>(KID_GACC_TO_DOUBLE)));
   k_gacc_to_double<NT><<<grid1(ctx->V, NT), NT, 0, ctx->stream>>>(ctx->Gacc, ctx->s64.G, ctx->V);
   CKL();
   TRY(timed_end(ctx));
   TRY(timed_begin(ctx, kid<double>(KID_TRANSFORM_FROM)));
-  k_transform_from<NT><<<grid1(ctx->V, NT), NT, 0, ctx->stream>>>(ctx->U0, ctx->s64.U, ctx->s64.G, ctx->L);
+  k_transform_from<NT><<<grid1(ctx->V, NT), NT, 0, ctx->stream>>>(ctx->U0, ctx->s64.U, ctx->s64.G, ctx->L,
+                                                                 write_base ? ctx->s32.U : nullptr);
   CKL();
+  ctx->resid_base_ready = write_base;
   return timed_end(ctx);
 }
 
@@ -729,10 +735,13 @@ lgf_status residual_begin(lgf_ctx *ctx) {
   TRY(setup_precision<float>(ctx, ctx->s32));
   TRY(alloc(ctx, &ctx->Rres, (size_t)36 * V * 2));
   TRY(alloc(ctx, &ctx->Kres, (size_t)9 * V * 2));
-  TRY(timed_begin(ctx, kid<float>(KID_RESIDUAL_BASE)));
-  k_narrow_link_planes<<<grid1((int64_t)4 * V, NT), NT, 0, ctx->stream>>>(ctx->s64.U, ctx->s32.U, V);
-  CKL();
-  TRY(timed_end(ctx));
+  if (!ctx->resid_base_ready) {
+    TRY(timed_begin(ctx, kid<float>(KID_RESIDUAL_BASE)));
+    k_narrow_link_planes<<<grid1((int64_t)4 * V, NT), NT, 0, ctx->stream>>>(ctx->s64.U, ctx->s32.U, V);
+    CKL();
+    TRY(timed_end(ctx));
+  }
+  ctx->resid_base_ready = false;
   CK(cudaMemsetAsync(ctx->Rres, 0, sizeof(float) * 72 * (size_t)V, ctx->stream));
   CK(cudaMemsetAsync(ctx->Kres, 0, sizeof(float) * 18 * (size_t)V, ctx->stream));
   Ctrl &c = ctx->ctrl_host;
@@ -758,15 +767,19 @@ lgf_status launch_iteration_residual(lgf_ctx *ctx, double alpha) {
   return launch_delta_residual(ctx, 1);
 }
 
-// End of the residual stage: G <- proj(1 + K) G, links rebuilt from the saved input in double, and
-// Delta, theta and F of the rebuilt links in double. Leaves the double state.
+// End of the residual stage: H = proj(1 + K) in double, U_h -> H U_h H^+(x + mu) in place by the double
+// update (small-step form: exact to FP64 rounding for H close to 1), and Delta, theta and F of the
+// rebuilt links in double. Leaves the double state.
 lgf_status residual_rebuild(lgf_ctx *ctx) {
-  TRY(timed_begin(ctx, kid<double>(KID_COMPOSE_RESIDUAL)));
-  k_compose_residual<NT><<<grid1(ctx->V, NT), NT, 0, ctx->stream>>>(ctx->Kres, ctx->s64.G, ctx->V);
+  State<double> &S = ctx->s64;
+  TRY(timed_begin(ctx, kid<double>(KID_RESIDUAL_GAUGE)));
+  k_residual_gauge<NT><<<grid1(ctx->V, NT), NT, 0, ctx->stream>>>(ctx->Kres, S.G, S.A, ctx->V);
   CKL();
   TRY(timed_end(ctx));
-  TRY(timed_begin(ctx, kid<double>(KID_TRANSFORM_FROM)));
-  k_transform_from<NT><<<grid1(ctx->V, NT), NT, 0, ctx->stream>>>(ctx->U0, ctx->s64.U, ctx->s64.G, ctx->L);
+  TRY(timed_begin(ctx, kid<double>(KID_RESIDUAL_REBUILD)));
+  k_update<double, NT_UPDATE64><<<dim3(grid1(ctx->V, NT_UPDATE64), 1, 1), NT_UPDATE64, update_smem_bytes<NT_UPDATE64>(),
+                                  ctx->stream>>>(S.U, S.G, S.A, ctx->L, ctx->ctrl, 0, kid<double>(KID_RESIDUAL_REBUILD),
+                                                 ctx->small_step ? 1 : 0);
   CKL();
   TRY(timed_end(ctx));
   Ctrl &c = ctx->ctrl_host;
@@ -1073,7 +1086,7 @@ lgf_status lgf_iterate(lgf_ctx *ctx, int max_new, double alpha, double eps, cons
       }
       if (mixed_float && (c.theta < thr || stalled)) {
         // hand over to double precision: rebuild the links from the input and G, then Delta, theta, F
-        TRY(handover(ctx));
+        TRY(handover(ctx, ctx->residual && !o.fft32_final));
         ctx->stage = LGF_FP64;
         ctx->prev_theta = 0;
         c.active = 1;

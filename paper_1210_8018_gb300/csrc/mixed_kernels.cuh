@@ -96,10 +96,12 @@ __global__ void __launch_bounds__(NT) k_gacc_to_double(const float *__restrict__
   for (int e = 0; e < 9; ++e) st(G64, (int64_t)e * V + s, m.e[e]);
 }
 
-// Udst_mu(x) = G(x) Usrc_mu(x) G^+(x + mu), double precision.
+// Udst_mu(x) = G(x) Usrc_mu(x) G^+(x + mu), double precision; with U32, rows 0-1 of the result also
+// rounded to float into the float link planes (the base of the residual stage).
 template <int NT>
 __global__ void __launch_bounds__(NT) k_transform_from(const double *__restrict__ Usrc, double *__restrict__ Udst,
-                                                      const double *__restrict__ G, Lattice L) {
+                                                      const double *__restrict__ G, Lattice L,
+                                                      float *__restrict__ U32) {
   const int64_t V = L.V;
   const int64_t s = (int64_t)blockIdx.x * NT + threadIdx.x;
   if (s >= V) return;
@@ -123,6 +125,11 @@ __global__ void __launch_bounds__(NT) k_transform_from(const double *__restrict_
     complete_row2(u);
 #pragma unroll
     for (int e = 0; e < 9; ++e) st(Udst, off + (int64_t)e * V + s, u.e[e]);
+    if (U32) {
+#pragma unroll
+      for (int e = 0; e < 6; ++e)
+        st(U32, (int64_t)(mu * 6 + e) * V + s, mkc(narrow_bits(u.e[e].r), narrow_bits(u.e[e].i)));
+    }
   }
 }
 
@@ -142,9 +149,10 @@ __global__ void k_set_identity(float *__restrict__ Gacc, int64_t V) {
 // quantity of the stage (a = g - 1, R, K with H = 1 + K the transformation gathered in the stage) is of
 // the size of the remaining gauge transformation, so its rounding is relative to that size and not to
 // the O(1) links: with changes of order 1e-4 the links are tracked to about 1e-11 and Delta to about
-// 1e-10, against entries of 3e-8 at theta = 1e-15. The stage ends with G <- proj(H) G in double and the
-// links rebuilt from the saved input in double (k_transform_from), so the result is exactly
-// gauge-equivalent to the input; theta is then recomputed in double.
+// 1e-10, against entries of 3e-8 at theta = 1e-15. The stage ends with H projected onto SU(3) in double
+// and U_h -> H U_h H^+(x + mu) by the double update (k_update, whose small-step form is exact to FP64
+// rounding for H close to 1), so the result stays exactly gauge-equivalent to the input; theta is then
+// recomputed in double.
 // ---------------------------------------------------------------------------------------------
 __device__ __forceinline__ bool residual_active(const Ctrl *ctrl) {
   return ctrl->active && ctrl->stage == kStageResidual;
@@ -239,8 +247,6 @@ __global__ void __launch_bounds__(NT) k_update_residual(const float *__restrict_
   count_run(ctrl, tkid);
   const int64_t s = (int64_t)blockIdx.x * NT + threadIdx.x;
   if (s >= V) return;
-  int c[4];
-  site_coords(L, s, c);
   m3<float> X, a, t;
   unpack_scaled(P, V, s, half_alpha, X);
   residual_step(X, a);
@@ -254,7 +260,8 @@ __global__ void __launch_bounds__(NT) k_update_residual(const float *__restrict_
 #pragma unroll 1
   for (int mu = 0; mu < 4; ++mu) {
     m3<float> b, u, r, w;
-    unpack_scaled(P, V, site_fwd(L, s, mu, c[mu]), half_alpha, X);
+    const int cmu = (int)(((unsigned)s / (unsigned)L.stride[mu]) % (unsigned)L.n[mu]);
+    unpack_scaled(P, V, site_fwd(L, s, mu, cmu), half_alpha, X);
     residual_step(X, b);
     float *rp = R + (int64_t)mu * 18 * V;
     load9(rp, V, s, r);
@@ -270,13 +277,14 @@ __global__ void __launch_bounds__(NT) k_update_residual(const float *__restrict_
   }
 }
 
-// G <- proj(1 + K) G in double: H projected onto SU(3) by Gram-Schmidt in FP64, then the product.
+// H = proj(1 + K) in double (Gram-Schmidt in FP64) into G, and a = H - 1 in double-float into A: the
+// gauge field with which the double update (small-step form) rebuilds U_h -> H U_h H^+(x + mu).
 template <int NT>
-__global__ void __launch_bounds__(NT) k_compose_residual(const float *__restrict__ K, double *__restrict__ G,
-                                                        int64_t V) {
+__global__ void __launch_bounds__(NT) k_residual_gauge(const float *__restrict__ K, double *__restrict__ G,
+                                                      float *__restrict__ A, int64_t V) {
   const int64_t s = (int64_t)blockIdx.x * NT + threadIdx.x;
   if (s >= V) return;
-  m3<double> h, g, t;
+  m3<double> h;
 #pragma unroll
   for (int e = 0; e < 9; ++e) {
     const cx<float> k = ldg(K, (int64_t)e * V + s);
@@ -286,10 +294,11 @@ __global__ void __launch_bounds__(NT) k_compose_residual(const float *__restrict
   h.e[4].r += 1.0;
   h.e[8].r += 1.0;
   reunitarize(h);
-  load9(G, V, s, g);
-  mul(h, g, t);
 #pragma unroll
-  for (int e = 0; e < 9; ++e) st(G, (int64_t)e * V + s, t.e[e]);
+  for (int e = 0; e < 9; ++e) {
+    st(G, (int64_t)e * V + s, h.e[e]);
+    st_a(A, (int64_t)e * V + s, minus_identity_split(h.e[e], e));
+  }
 }
 
 }  // namespace lgf
