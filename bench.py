@@ -124,8 +124,9 @@ def algorithmic(kernel, dims):
     b, f, prec = work_model(kernel, dims)
     name = kernel.rsplit(".", 1)[0]
     if prec == "f64":
-        kind = {"gauge_update": "fp32", "residual_rebuild": "fp32", "handover_transform": "fp64",
-                "gacc_to_double": "fp64", "residual_gauge": "fp64"}.get(name)
+        # (the handover transform runs in 61-bit fixed point on the integer pipe: bytes only)
+        kind = {"gauge_update": "fp32", "residual_rebuild": "fp32", "gacc_to_double": "fp64",
+                "residual_gauge": "fp64"}.get(name)
     else:
         kind = None
     return b, (f if kind else 0), kind

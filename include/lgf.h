@@ -47,7 +47,8 @@ typedef enum {
   LGF_FP64 = 0,  /* every step at double precision: FP64 links and sums (equivalent forms of some
                     steps are listed at lgf_create)                                              */
   LGF_MIXED = 1, /* float links, FFTs and updates (double reductions) until theta <= theta_switch,
-                    then a double-precision handover and double precision to theta < eps         */
+                    then a double-precision handover, float iterations on the residual of the
+                    handover links, and the double links rebuilt exactly, to theta < eps        */
   LGF_FP32 = 2   /* float links, FFTs and updates throughout (double reductions)                 */
 } lgf_precision;
 
@@ -81,7 +82,11 @@ void lgf_default_options(lgf_options *opt);
  * is small: g = 1 + a formed in double-float when every |(alpha/2) Delta-tilde| < 2^-8, and rows 0-1
  * of the update as U + [a U + (U + a U) b^+] (a = g(x) - 1, b = g(x+mu) - 1) with the bracket in
  * double-float when every |a|, |b| < 2^-7 (row 2 = conj(row0 x row1) in FP64 in both forms). Their
- * errors are at the level of the FP64 rounding of the plain forms. */
+ * errors are at the level of the FP64 rounding of the plain forms. Two switches concern LGF_MIXED:
+ * LGF_HANDOVER_FP64=1 forms the handover links G U0 G^+(x+mu) in FP64 instead of in 64-bit fixed
+ * point with 61 fractional bits (exact to FP64 rounding either way), and LGF_RESIDUAL=0 runs double
+ * iterations after the handover instead of the residual stage (float iterations on U = U_h + R, with
+ * R the float change since the handover, then the double links rebuilt exactly). */
 lgf_status lgf_create(int Nx, int Ny, int Nz, int Nt, lgf_ctx **out);
 
 /* Release every resource of the context (NULL is accepted). */

@@ -223,8 +223,8 @@ lgf_status handover_one(lgf_ctx *g, int j) {
   lgf_ctx *ctx = g;
   k_gacc_to_double<NT><<<grid1(g->V, NT), NT, 0, g->stream>>>(cfg_gacc(g->Gacc, g, j), cfg_mat(g->s64.G, g, j), g->V);
   CKL();
-  k_transform_from<NT><<<grid1(g->V, NT), NT, 0, g->stream>>>(cfg_links(g->U0, g, j), cfg_links(g->s64.U, g, j),
-                                                              cfg_mat(g->s64.G, g, j), g->L, nullptr);
+  k_transform_from_q<NT><<<grid1(g->V, NT), NT, 0, g->stream>>>(cfg_links(g->U0, g, j), cfg_links(g->s64.U, g, j),
+                                                                cfg_mat(g->s64.G, g, j), g->L, nullptr);
   CKL();
   return LGF_OK;
 }

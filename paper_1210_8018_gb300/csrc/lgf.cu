@@ -141,6 +141,7 @@ struct lgf_ctx {
   bool fft_df64 = true;      // double state: Fourier filter in df64 (LGF_FFT_NATIVE_F64=1: IEEE double)
   bool residual = true;      // mixed: residual stage after the handover (LGF_RESIDUAL=0: double iterations)
   bool resid_off = false;    // this load: a rebuild made no progress, the double stage continues
+  bool handover_fp64 = false;  // mixed handover transform in FP64 instead of 61-bit fixed point
   bool resid_base_ready = false;  // the float link planes hold the double links rounded (by the handover)
   double resid_F = 0, resid_theta0 = 0;  // F and theta of the residual stage's base links
   bool small_step = true;    // double g and update: small-step forms where they apply (LGF_SMALL_STEP=0: never)
@@ -704,8 +705,12 @@ lgf_status handover(lgf_ctx *ctx, bool write_base = false) {
   CKL();
   TRY(timed_end(ctx));
   TRY(timed_begin(ctx, kid<double>(KID_TRANSFORM_FROM)));
-  k_transform_from<NT><<<grid1(ctx->V, NT), NT, 0, ctx->stream>>>(ctx->U0, ctx->s64.U, ctx->s64.G, ctx->L,
-                                                                 write_base ? ctx->s32.U : nullptr);
+  if (ctx->handover_fp64)
+    k_transform_from<NT><<<grid1(ctx->V, NT), NT, 0, ctx->stream>>>(ctx->U0, ctx->s64.U, ctx->s64.G, ctx->L,
+                                                                   write_base ? ctx->s32.U : nullptr);
+  else
+    k_transform_from_q<NT><<<grid1(ctx->V, NT), NT, 0, ctx->stream>>>(ctx->U0, ctx->s64.U, ctx->s64.G, ctx->L,
+                                                                     write_base ? ctx->s32.U : nullptr);
   CKL();
   ctx->resid_base_ready = write_base;
   return timed_end(ctx);
@@ -905,6 +910,8 @@ static lgf_status create_ctx(const int n[4], int nb, lgf_ctx **out) {
     ctx->small_step = !(ss && ss[0] == '0');
     const char *rs = std::getenv("LGF_RESIDUAL");
     ctx->residual = !(rs && rs[0] == '0');
+    const char *hf = std::getenv("LGF_HANDOVER_FP64");
+    ctx->handover_fp64 = hf && hf[0] == '1';
   }
   cudaDeviceGetAttribute(&ctx->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
   // p^2 tables (position -> 4 sin^2(pi k / N)) and the filter scale p^2_max / V

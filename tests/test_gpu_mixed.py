@@ -99,6 +99,28 @@ def test_mixed_float_stage_hands_over_when_theta_stalls(lgf):
     assert oracle.theta(oracle.delta(Uf)) < 1e-15
 
 
+def test_handover_fixed_point_matches_fp64(lgf, monkeypatch):
+    """The handover links G U0 G^+(x+mu) formed in 61-bit fixed point agree with the FP64 product to a few
+    units of the FP64 rounding, and both are gauge-equivalent to the input."""
+    dims = (8, 8, 4, 6)
+    U = synth.config(dims, 9, 0.6)
+
+    def stored():
+        with lgf.Lattice(dims) as lat:
+            lat.load(U, "mixed")
+            lat.iterate(7, 0.08, 1e-15, theta_switch=1e-30)
+            out = np.empty_like(U)
+            lat.store(out)
+        return out
+    Uq = stored()
+    monkeypatch.setenv("LGF_HANDOVER_FP64", "1")
+    Ud = stored()
+    assert float(np.abs(Uq - Ud).max()) < 1e-15
+    for Us in (Uq, Ud):
+        assert abs(oracle.plaquette(Us) - oracle.plaquette(U)) < 1e-14
+        assert oracle.unitarity_violation(Us) < 1e-13
+
+
 def test_fp32_precision_fix_reaches_float_floor(lgf):
     dims = (8, 8, 8, 8)
     U = synth.config(dims, 1, 0.3)
