@@ -219,12 +219,54 @@ template <typename T> lgf_status delta_one(lgf_ctx *g, State<T> &S, int j) {
   });
 }
 
-lgf_status handover_one(lgf_ctx *g, int j) {
+// Handover of configuration j; with base, rows 0-1 of the new links rounded to float also go to its float
+// link planes (the base of its residual stage).
+lgf_status handover_one(lgf_ctx *g, int j, bool base) {
   lgf_ctx *ctx = g;
   k_gacc_to_double<NT><<<grid1(g->V, NT), NT, 0, g->stream>>>(cfg_gacc(g->Gacc, g, j), cfg_mat(g->s64.G, g, j), g->V);
   CKL();
   k_transform_from_q<NT><<<grid1(g->V, NT), NT, 0, g->stream>>>(cfg_links(g->U0, g, j), cfg_links(g->s64.U, g, j),
-                                                                cfg_mat(g->s64.G, g, j), g->L, nullptr);
+                                                                cfg_mat(g->s64.G, g, j), g->L,
+                                                                base ? cfg_links(g->s32.U, g, j) : nullptr);
+  CKL();
+  return LGF_OK;
+}
+
+// Residual stage of configuration j (see lgf_iterate), entered after its double Delta, theta and F: the
+// base links (narrowed from the double links unless the handover wrote them), R = K = 0, the loop
+// control's transition (on the device) and the initial Delta.
+lgf_status enter_residual_one(lgf_ctx *g, int j, double eps, bool narrow) {
+  lgf_ctx *ctx = g;
+  const int64_t V = g->V;
+  if (narrow) {
+    k_narrow_link_planes<<<grid1(4 * V, NT), NT, 0, g->stream>>>(cfg_links(g->s64.U, g, j), cfg_links(g->s32.U, g, j), V);
+    CKL();
+  }
+  CK(cudaMemsetAsync(g->Rres + (int64_t)j * 72 * V, 0, sizeof(float) * 72 * (size_t)V, g->stream));
+  CK(cudaMemsetAsync(g->Kres + (int64_t)j * 18 * V, 0, sizeof(float) * 18 * (size_t)V, g->stream));
+  k_enter_residual<<<1, 1, 0, g->stream>>>(g->ctrl + j, 0.8 * eps);
+  CKL();
+  return with_fft_type<double>(g, [&](auto tag) -> lgf_status {
+    using FT = decltype(tag);
+    k_delta_residual<NT, FT><<<dim3(g->nblocks_site, 1, 1), NT, 0, g->stream>>>(
+        g->Rres + (int64_t)j * 72 * V, reinterpret_cast<const FT *>(cfg_packed(g->s64.P, g, j)),
+        cfg_packed(g->s32.P, g, j), g->partials + (int64_t)j * 2 * g->nblocks_site, g->ctrl + j, g->L, 0, 0);
+    CKL();
+    return LGF_OK;
+  });
+}
+
+// End of the residual stage of configuration j: H = proj(1 + K) in double and the double links rebuilt by
+// the double update (small-step form), in place.
+lgf_status rebuild_one(lgf_ctx *g, int j) {
+  lgf_ctx *ctx = g;
+  const int64_t V = g->V;
+  float *A = g->s64.A + (int64_t)j * 9 * V * 4;
+  k_residual_gauge<NT><<<grid1(V, NT), NT, 0, g->stream>>>(g->Kres + (int64_t)j * 18 * V, cfg_mat(g->s64.G, g, j), A, V);
+  CKL();
+  k_update<double, NT_UPDATE64><<<dim3(grid1(V, NT_UPDATE64), 1, 1), NT_UPDATE64, update_smem_bytes<NT_UPDATE64>(),
+                                  g->stream>>>(cfg_links(g->s64.U, g, j), cfg_mat(g->s64.G, g, j), A, g->L, g->ctrl + j,
+                                               0, 0, g->small_step ? 1 : 0);
   CKL();
   return LGF_OK;
 }
@@ -315,6 +357,10 @@ lgf_status lgf_batch_fix(lgf_batch *b, double *const *links, double alpha, doubl
       BTRY(g, setup_precision<float>(g, g->s32));
       BTRY(g, alloc(g, &g->Gacc, (size_t)g->nb * 6 * g->V * 2));
       if (prec == LGF_MIXED) BTRY(g, alloc(g, &g->U0, (size_t)g->nb * 4 * 9 * g->V * 2));
+      if (prec == LGF_MIXED && g->residual) {
+        BTRY(g, alloc(g, &g->Rres, (size_t)g->nb * 72 * g->V));
+        BTRY(g, alloc(g, &g->Kres, (size_t)g->nb * 18 * g->V));
+      }
       TuneEntry e;
       if (b->autotune) BTRY(g, autotune_fft<float>(g, g->s32, &e));
       b->tuned[1] += tune_key<float>(g) + "=" + (b->autotune ? e.plan + "/" + std::to_string(e.C) : "default") + " ";
@@ -379,6 +425,15 @@ lgf_status lgf_batch_fix(lgf_batch *b, double *const *links, double alpha, doubl
             return bfail(b, st, g->err);
           }
         }
+        if (prec == LGF_MIXED && g->residual) {
+          const lgf_status st = launch_iteration_residual(g, alpha);
+          launches += (int)g->s32.passes.size() + 2;
+          if (st != LGF_OK) {
+            cudaGraph_t junk;
+            cudaStreamEndCapture(b->stream, &junk);
+            return bfail(b, st, g->err);
+          }
+        }
       }
     cudaGraph_t graph;
     BCK(cudaStreamEndCapture(b->stream, &graph));
@@ -390,10 +445,17 @@ lgf_status lgf_batch_fix(lgf_batch *b, double *const *links, double alpha, doubl
     b->launches_per_replay = launches;
   }
   b->graph_replays = 0;
-  // replay until every configuration has stopped; hand over mixed configurations at theta_switch, or
-  // when a replay of the float stage did not lower theta (the resolution of float links is reached)
+  // replay until every configuration has stopped. Mixed configurations hand over at theta_switch, or
+  // when a replay of the float stage did not lower theta (the resolution of float links is reached),
+  // then run the residual stage; at its end (or when a replay of it did not lower theta) the double
+  // links are rebuilt and theta is recomputed in double, and the stage starts again from the rebuilt
+  // links while theta >= eps -- after three rebuilds double iterations take over instead.
   std::vector<std::vector<std::pair<double, int>>> last(b->groups.size());
-  for (size_t k = 0; k < b->groups.size(); ++k) last[k].assign(b->groups[k]->nb, {0.0, -1});
+  std::vector<std::vector<int>> rebuilds(b->groups.size());
+  for (size_t k = 0; k < b->groups.size(); ++k) {
+    last[k].assign(b->groups[k]->nb, {0.0, -1});
+    rebuilds[k].assign(b->groups[k]->nb, 0);
+  }
   for (;;) {
     bool pending = false;
     for (size_t k = 0; k < b->groups.size(); ++k) {
@@ -406,19 +468,44 @@ lgf_status lgf_batch_fix(lgf_batch *b, double *const *links, double alpha, doubl
       for (int j = 0; j < g->nb; ++j) {
         Ctrl &c = host[k][j];
         if (c.status == 5) continue;
-        const bool stalled = prec == LGF_MIXED && c.stage == 0 && c.active && last[k][j].second >= 0 &&
-                             last[k][j].second < c.iters && !(c.theta < last[k][j].first);
+        const bool residual = prec == LGF_MIXED && g->residual;
+        const bool stalled = prec == LGF_MIXED && (c.stage == 0 || c.stage == kStageResidual) && c.active &&
+                             last[k][j].second >= 0 && last[k][j].second < c.iters &&
+                             !(c.theta < last[k][j].first);
         last[k][j] = {c.theta, c.iters};
         if (c.active && !stalled) {
           pending = true;
         } else if (prec == LGF_MIXED && c.stage == 0 && (c.theta < thr0 || stalled) && c.iters < c.limit) {
           BTRY(g, setup_precision<double>(g, g->s64));
-          BTRY(g, handover_one(g, j));
+          BTRY(g, handover_one(g, j, residual));
           c.stage = 1;
           c.threshold = eps;
           c.active = 1;
           BCK(cudaMemcpyAsync(g->ctrl + j, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, b->stream));
           BTRY(g, delta_one<double>(g, g->s64, j));
+          if (residual) BTRY(g, enter_residual_one(g, j, eps, false));
+          last[k][j] = {0.0, -1};
+          pending = true;
+        } else if (c.stage == kStageResidual) {
+          BTRY(g, rebuild_one(g, j));
+          c.stage = 1;
+          c.threshold = eps;
+          c.active = 1;
+          BCK(cudaMemcpyAsync(g->ctrl + j, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, b->stream));
+          BTRY(g, delta_one<double>(g, g->s64, j));
+          k_set_active<<<1, 1, 0, b->stream>>>(g->ctrl + j, 0);  // the host decides what follows
+          BCK(cudaGetLastError());
+          ++rebuilds[k][j];
+          last[k][j] = {0.0, -1};
+          pending = true;
+        } else if (residual && c.stage == 1 && rebuilds[k][j] > 0 && !(c.theta < eps) && c.iters < c.limit) {
+          if (rebuilds[k][j] < 4) {
+            BTRY(g, enter_residual_one(g, j, eps, true));
+          } else {
+            c.active = 1;
+            BCK(cudaMemcpyAsync(g->ctrl + j, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, b->stream));
+          }
+          last[k][j] = {0.0, -1};
           pending = true;
         }
       }
@@ -447,7 +534,7 @@ lgf_status lgf_batch_fix(lgf_batch *b, double *const *links, double alpha, doubl
       BTRY(g, from_planes<double>(g, cfg_links(g->s64.U, g, j), dst, 4));
     } else if (prec == LGF_MIXED) {
       BTRY(g, setup_precision<double>(g, g->s64));
-      BTRY(g, handover_one(g, j));
+      BTRY(g, handover_one(g, j, false));
       BTRY(g, from_planes<double>(g, cfg_links(g->s64.U, g, j), dst, 4));
     } else {
       BTRY(g, from_planes<float>(g, cfg_links(g->s32.U, g, j), dst, 4));

@@ -143,7 +143,7 @@ struct lgf_ctx {
   bool resid_off = false;    // this load: a rebuild made no progress, the double stage continues
   bool handover_fp64 = false;  // mixed handover transform in FP64 instead of 61-bit fixed point
   bool resid_base_ready = false;  // the float link planes hold the double links rounded (by the handover)
-  double resid_F = 0, resid_theta0 = 0;  // F and theta of the residual stage's base links
+  double resid_theta0 = 0;  // theta of the residual stage's base links
   bool small_step = true;    // double g and update: small-step forms where they apply (LGF_SMALL_STEP=0: never)
   int fixed_cols[2] = {0, 0};  // column width of the specialised passes (double, float); 0 = default
   double prev_theta = 0;  // theta and iteration count at the previous chunk boundary
@@ -726,9 +726,9 @@ lgf_status launch_delta_residual(lgf_ctx *ctx, int counts_update) {
   TRY(timed_begin(ctx, kid<float>(KID_DELTA_RESIDUAL)));
   TRY(with_fft_type<double>(ctx, [&](auto tag) -> lgf_status {
     using FT = decltype(tag);
-    k_delta_residual<NT, FT><<<ctx->nblocks_site, NT, 0, ctx->stream>>>(
+    k_delta_residual<NT, FT><<<dim3(ctx->nblocks_site, 1, ctx->nb), NT, 0, ctx->stream>>>(
         ctx->Rres, reinterpret_cast<const FT *>(ctx->s64.P), ctx->s32.P, ctx->partials, ctx->ctrl, ctx->L,
-        ctx->resid_F, counts_update, kid<float>(KID_DELTA_RESIDUAL));
+        counts_update, kid<float>(KID_DELTA_RESIDUAL));
     CKL();
     return LGF_OK;
   }));
@@ -750,10 +750,10 @@ lgf_status residual_begin(lgf_ctx *ctx) {
   CK(cudaMemsetAsync(ctx->Rres, 0, sizeof(float) * 72 * (size_t)V, ctx->stream));
   CK(cudaMemsetAsync(ctx->Kres, 0, sizeof(float) * 18 * (size_t)V, ctx->stream));
   Ctrl &c = ctx->ctrl_host;
-  ctx->resid_F = c.F;
   ctx->resid_theta0 = c.theta;
   ctx->stage = kHostStageResidual;
   ctx->prev_theta = 0;
+  c.f_base = c.F;
   c.stage = kStageResidual;
   c.active = 1;
   TRY(write_ctrl(ctx));
@@ -762,9 +762,9 @@ lgf_status residual_begin(lgf_ctx *ctx) {
 }
 
 lgf_status launch_iteration_residual(lgf_ctx *ctx, double alpha) {
-  TRY(launch_filter<float>(ctx, ctx->s32, ctx->s32.P, 2));
+  TRY(launch_filter<float>(ctx, ctx->s32, ctx->s32.P, 3));
   TRY(timed_begin(ctx, kid<float>(KID_UPDATE_RESIDUAL)));
-  k_update_residual<NT><<<grid1(ctx->V, NT), NT, 0, ctx->stream>>>(ctx->s32.U, ctx->Rres, ctx->Kres, ctx->s32.P,
+  k_update_residual<NT><<<dim3(grid1(ctx->V, NT), 1, ctx->nb), NT, 0, ctx->stream>>>(ctx->s32.U, ctx->Rres, ctx->Kres, ctx->s32.P,
                                                                  (float)(0.5 * alpha), ctx->L, ctx->ctrl,
                                                                  kid<float>(KID_UPDATE_RESIDUAL));
   CKL();

@@ -284,13 +284,22 @@ template <typename T> __device__ __forceinline__ void load9(const T *plane, int6
   for (int e = 0; e < 9; ++e) u.e[e] = ldg(plane, (int64_t)e * V + s);
 }
 
-// Delta = Delta(U_h) + Delta(R) (packed, float), theta and F = F_h + sum Re Tr R / (12 V) (a1/a2).
-// Ph: packed Delta(U_h) in the double state's FFT type PT.
+// Delta = Delta(U_h) + Delta(R) (packed, float), theta and F = F(U_h) + sum Re Tr R / (12 V) (a1/a2),
+// F(U_h) from the loop control. Ph: packed Delta(U_h) in the double state's FFT type PT. blockIdx.z:
+// configuration of a batch group.
 template <int NT, typename PT>
 __global__ void __launch_bounds__(NT) k_delta_residual(const float *__restrict__ R, const PT *__restrict__ Ph,
                                                       float *__restrict__ P, double *partials, Ctrl *ctrl, Lattice L,
-                                                      double F_h, int counts_update, int tkid) {
+                                                      int counts_update, int tkid) {
   const int64_t V = L.V;
+  {
+    const int cfg = blockIdx.z;
+    R += (int64_t)cfg * 36 * V * 2;
+    Ph += (int64_t)cfg * 4 * V * 2;
+    P += (int64_t)cfg * 4 * V * 2;
+    partials += (int64_t)cfg * 2 * gridDim.x;
+    ctrl += cfg;
+  }
   if (!residual_active(ctrl)) return;
   count_run(ctrl, tkid);
   double th = 0.0, f = 0.0;
@@ -330,8 +339,19 @@ __global__ void __launch_bounds__(NT) k_delta_residual(const float *__restrict__
 #pragma unroll
     for (int q = 0; q < 4; ++q) st(P, (int64_t)q * V + s, mkc(d[2 * q], d[2 * q + 1]));
   }
-  reduce_and_finalize<NT>(th, f, partials, ctrl, V, counts_update, F_h);
+  reduce_and_finalize<NT>(th, f, partials, ctrl, V, counts_update, ctrl->f_base);
 }
+
+// Loop control of one configuration entering the residual stage (after its double Delta, theta and F):
+// F of the base, the stage and its threshold, active.
+__global__ void k_enter_residual(Ctrl *ctrl, double threshold) {
+  ctrl->f_base = ctrl->F;
+  ctrl->stage = kStageResidual;
+  ctrl->threshold = threshold;
+  ctrl->active = 1;
+}
+
+__global__ void k_set_active(Ctrl *ctrl, int active) { ctrl->active = active; }
 
 // a = g - 1 with g the SU(3) projection of 1 + X, in float: the small-step form when every |X| < 2^-8,
 // else Gram-Schmidt of 1 + X minus the identity (large steps, where float rounding of a is harmless).
@@ -361,6 +381,14 @@ __global__ void __launch_bounds__(NT) k_update_residual(const float *__restrict_
                                                        float *__restrict__ K, const float *__restrict__ P,
                                                        float half_alpha, Lattice L, const Ctrl *ctrl, int tkid) {
   const int64_t V = L.V;
+  {
+    const int cfg = blockIdx.z;
+    B += (int64_t)cfg * 4 * link_plane_stride<float>(V);
+    R += (int64_t)cfg * 36 * V * 2;
+    K += (int64_t)cfg * 9 * V * 2;
+    P += (int64_t)cfg * 4 * V * 2;
+    ctrl += cfg;
+  }
   if (!residual_active(ctrl)) return;
   count_run(ctrl, tkid);
   const int64_t s = (int64_t)blockIdx.x * NT + threadIdx.x;

@@ -30,6 +30,7 @@ struct Lattice {
 struct Ctrl {
   double theta, F;       // values after the latest Delta evaluation
   double threshold;      // iterate while theta >= threshold
+  double f_base;         // residual stage: F of the base links (F of the stage = f_base + residual part)
   int iters;             // gauge updates applied since load
   int limit;             // stop when iters reaches this
   int active;            // 1 while the loop runs; kernels return at once when 0
@@ -79,9 +80,11 @@ template <typename T> __device__ __forceinline__ bool stage_active(const Ctrl *c
   return ctrl->active && ctrl->stage == (sizeof(T) == 8 ? 1 : 0);
 }
 // check: 0 run unconditionally; 1 run if the loop is active in this kernel's precision; 2 run if the
-// loop is active whatever the stage (a float FFT serving the double stage).
+// loop is active whatever the stage (a float FFT serving the double stage); 3 run if the loop is active
+// in the residual stage (the float FFT of that stage).
 template <typename T> __device__ __forceinline__ bool should_run(const Ctrl *ctrl, int check) {
   if (!check) return true;
+  if (check == 3) return ctrl->active && ctrl->stage == kStageResidual;
   return check == 2 ? ctrl->active != 0 : stage_active<T>(ctrl);
 }
 

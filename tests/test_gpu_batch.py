@@ -78,3 +78,17 @@ def test_batch_mixed_float_stage_hands_over_when_theta_stalls(lgf):
         assert r["status"] == lgf.LGF_OK and r["theta"] < 1e-15 and r["iters"] < 1000
         assert abs(oracle.plaquette(Uf) - oracle.plaquette(U)) < 1e-14
         assert oracle.theta(oracle.delta(Uf)) < 1e-15
+
+
+def test_batch_mixed_matches_single_contexts(lgf):
+    """The ensemble's mixed schedule (float stage, handover, residual stage, rebuild) gives each configuration
+    the fixed point and, within the replay granularity, the iteration count of a single-context fix."""
+    Us = configs()
+    with lgf.Batch(SHAPES) as b:
+        res = b.fix([U.copy() for U in Us], 0.08, 1e-15, "mixed")
+    for U, r in zip(Us, res):
+        with lgf.Lattice(oracle.dims_of_links(U)) as lat:
+            r1 = lat.fix(U.copy(), 0.08, 1e-15, "mixed")
+        assert r["status"] == lgf.LGF_OK and r1["converged"] and r["theta"] < 1e-15
+        assert abs(r1["iters"] - r["iters"]) <= 2, (r, r1)
+        assert abs(r1["F"] - r["F"]) <= 1e-12 * abs(r1["F"])
