@@ -240,7 +240,8 @@ def config_of(args, dims, path):
                                              args.eps, args.seed, path),
             "lattice": list(dims), "precision": args.precision, "theta_switch": args.theta_switch,
             "step": "one complete gauge fixing (Algorithm 1 until theta < 1e-15)",
-            "l2": "no flush: links 9.66 GB per step >> 129 MB L2" if np.prod(dims) >= 2 ** 20 else "small lattice",
+            "l2": ("no flush: links %.3g GB per step >> 129 MB L2" % (int(np.prod(dims)) * 576 / 1e9)
+                   if np.prod(dims) >= 2 ** 20 else "small lattice"),
             "parallelism": "replicas"}
 
 
