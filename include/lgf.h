@@ -82,11 +82,15 @@ void lgf_default_options(lgf_options *opt);
  * is small: g = 1 + a formed in double-float when every |(alpha/2) Delta-tilde| < 2^-8, and rows 0-1
  * of the update as U + [a U + (U + a U) b^+] (a = g(x) - 1, b = g(x+mu) - 1) with the bracket in
  * double-float when every |a|, |b| < 2^-7 (row 2 = conj(row0 x row1) in FP64 in both forms). Their
- * errors are at the level of the FP64 rounding of the plain forms. Two switches concern LGF_MIXED:
- * LGF_HANDOVER_FP64=1 forms the handover links G U0 G^+(x+mu) in FP64 instead of in 64-bit fixed
- * point with 61 fractional bits (exact to FP64 rounding either way), and LGF_RESIDUAL=0 runs double
- * iterations after the handover instead of the residual stage (float iterations on U = U_h + R, with
- * R the float change since the handover, then the double links rebuilt exactly). */
+ * errors are at the level of the FP64 rounding of the plain forms. Three switches concern the float
+ * stages and LGF_MIXED: LGF_REUNIT_FP64=1 makes the periodic projection of the float links and of the
+ * accumulated transformation onto SU(3) double precision instead of float; LGF_HANDOVER_FP64=1 forms the
+ * handover links G U0 G^+(x+mu) in FP64 instead of in 64-bit fixed point with 61 fractional bits (exact
+ * to FP64 rounding either way); and LGF_RESIDUAL=0 runs double iterations after the handover instead of
+ * the residual stage (float iterations on U = U_h + R, with R the float change since the handover, then
+ * the double links rebuilt exactly). With LGF_REUNIT_FP64=1, LGF_RESIDUAL=0 and theta_switch = 1e-8
+ * the mixed schedule is: float iterations with double reductions and periodic double reprojection until
+ * theta <= 1e-8, the handover, and double iterations to theta < eps. */
 lgf_status lgf_create(int Nx, int Ny, int Nz, int Nt, lgf_ctx **out);
 
 /* Release every resource of the context (NULL is accepted). */

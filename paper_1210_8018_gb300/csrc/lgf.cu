@@ -142,6 +142,7 @@ struct lgf_ctx {
   bool residual = true;      // mixed: residual stage after the handover (LGF_RESIDUAL=0: double iterations)
   bool resid_off = false;    // this load: a rebuild made no progress, the double stage continues
   bool handover_fp64 = false;  // mixed handover transform in FP64 instead of 61-bit fixed point
+  bool reunit_fp64 = false;    // float stages: periodic projection onto SU(3) in double instead of float
   bool resid_base_ready = false;  // the float link planes hold the double links rounded (by the handover)
   double resid_theta0 = 0;  // theta of the residual stage's base links
   bool small_step = true;    // double g and update: small-step forms where they apply (LGF_SMALL_STEP=0: never)
@@ -668,13 +669,14 @@ lgf_status launch_iteration_float(lgf_ctx *ctx, double alpha, bool reunit) {
   TRY(launch_filter<float>(ctx, S, S.P, 1));
   const int kidx = kid<float>(reunit ? KID_UPDATE_FUSED_REUNIT : KID_UPDATE_FUSED);
   TRY(timed_begin(ctx, kidx));
-  if (reunit)
-    k_update_fused_f32<NT, true><<<dim3(grid1(ctx->V, NT), 1, ctx->nb), NT, 0, ctx->stream>>>(S.U, S.P, ctx->Gacc, (float)(0.5 * alpha),
-                                                                             ctx->L, ctx->ctrl, kidx);
+  const dim3 grid(grid1(ctx->V, NT), 1, ctx->nb);
+  const float ha = (float)(0.5 * alpha);
+  if (reunit && ctx->reunit_fp64)
+    k_update_fused_f32<NT, 2><<<grid, NT, 0, ctx->stream>>>(S.U, S.P, ctx->Gacc, ha, ctx->L, ctx->ctrl, kidx);
+  else if (reunit)
+    k_update_fused_f32<NT, 1><<<grid, NT, 0, ctx->stream>>>(S.U, S.P, ctx->Gacc, ha, ctx->L, ctx->ctrl, kidx);
   else
-    k_update_fused_f32<NT, false><<<dim3(grid1(ctx->V, NT), 1, ctx->nb), NT, 0, ctx->stream>>>(S.U, S.P, ctx->Gacc,
-                                                                              (float)(0.5 * alpha), ctx->L, ctx->ctrl,
-                                                                              kidx);
+    k_update_fused_f32<NT, 0><<<grid, NT, 0, ctx->stream>>>(S.U, S.P, ctx->Gacc, ha, ctx->L, ctx->ctrl, kidx);
   CKL();
   TRY(timed_end(ctx));
   return launch_delta<float>(ctx, S, 1, 1);
@@ -912,6 +914,8 @@ static lgf_status create_ctx(const int n[4], int nb, lgf_ctx **out) {
     ctx->residual = !(rs && rs[0] == '0');
     const char *hf = std::getenv("LGF_HANDOVER_FP64");
     ctx->handover_fp64 = hf && hf[0] == '1';
+    const char *rf = std::getenv("LGF_REUNIT_FP64");
+    ctx->reunit_fp64 = rf && rf[0] == '1';
   }
   cudaDeviceGetAttribute(&ctx->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
   // p^2 tables (position -> 4 sin^2(pi k / N)) and the filter scale p^2_max / V

@@ -17,13 +17,25 @@ __device__ __forceinline__ void gauge_from_packed(const float *P, int64_t V, int
   reunitarize(g);
 }
 
+// SU(3) projection of a float matrix (rows 0-1 given) in double precision; float <-> double by integer
+// operations (the conversion instructions would share the FP64 pipe with the projection).
+__device__ __forceinline__ void reunitarize_fp64(m3<float> &u) {
+  m3<double> d;
+#pragma unroll
+  for (int e = 0; e < 6; ++e) d.e[e] = {widen_bits(u.e[e].r), widen_bits(u.e[e].i)};
+  reunitarize(d);
+#pragma unroll
+  for (int e = 0; e < 6; ++e) u.e[e] = {narrow_bits(d.e[e].r), narrow_bits(d.e[e].i)};
+}
+
 // Float-stage update with g rebuilt in registers: forms g(x) and the four g(x + mu) from the packed
 // Delta-tilde (no g field in memory), accumulates Gacc(x) <- g(x) Gacc(x) and applies
 // U_mu(x) -> g(x) U_mu(x) g^+(x + mu). With REUNIT the new G and the new links are projected onto SU(3)
-// before they are stored (the periodic reunitarisation of the float stage). The projection is done in
-// float: it only has to remove the drift from unitarity that float rounding accumulates between
-// projections, and the handover rebuilds double links from the saved input and a G projected in double.
-template <int NT, bool REUNIT>
+// before they are stored (the periodic reunitarisation of the float stage): REUNIT 1 projects in float,
+// which only has to remove the drift from unitarity that float rounding accumulates between projections
+// (the handover rebuilds double links from the saved input and a G projected in double); REUNIT 2
+// projects in double precision.
+template <int NT, int REUNIT>
 __global__ void __launch_bounds__(NT) k_update_fused_f32(float *__restrict__ U, const float *__restrict__ P,
                                                         float *__restrict__ Gacc, float half_alpha, Lattice L,
                                                         const Ctrl *ctrl, int tkid) {
@@ -48,7 +60,8 @@ __global__ void __launch_bounds__(NT) k_update_fused_f32(float *__restrict__ U, 
   for (int e = 0; e < 6; ++e) a.e[e] = ld(Gacc, (int64_t)e * V + s);
   complete_row2(a);
   mul_rows01(gx, a, t);
-  if constexpr (REUNIT) reunitarize(t);
+  if constexpr (REUNIT == 1) reunitarize(t);
+  if constexpr (REUNIT == 2) reunitarize_fp64(t);
 #pragma unroll
   for (int e = 0; e < 6; ++e) st(Gacc, (int64_t)e * V + s, t.e[e]);
 #pragma unroll 1
@@ -60,7 +73,8 @@ __global__ void __launch_bounds__(NT) k_update_fused_f32(float *__restrict__ U, 
     gauge_from_packed(P, V, sf, half_alpha, gy);
     mul_rows01(gx, u, t);
     mul_adj_rows01(t, gy, u);
-    if constexpr (REUNIT) reunitarize(u);
+    if constexpr (REUNIT == 1) reunitarize(u);
+    if constexpr (REUNIT == 2) reunitarize_fp64(u);
     store_link(plane, V, s, u);
   }
 }

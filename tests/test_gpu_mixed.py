@@ -121,6 +121,30 @@ def test_handover_fixed_point_matches_fp64(lgf, monkeypatch):
         assert oracle.unitarity_violation(Us) < 1e-13
 
 
+def test_mixed_schedule_as_specified(lgf, monkeypatch):
+    """The mixed schedule in its plainest form (float links, FFTs and updates with double reductions and a
+    double-precision reprojection every 16 iterations until theta <= 1e-8, the handover, double iterations
+    to theta < 1e-15): theta, F and the plaquette against the FP64 oracle and the double path."""
+    monkeypatch.setenv("LGF_REUNIT_FP64", "1")
+    monkeypatch.setenv("LGF_RESIDUAL", "0")
+    dims = (16, 16, 16, 16)
+    U = synth.config(dims, 7, 0.6)
+    Um = U.copy()
+    with lgf.Lattice(dims) as lat:
+        lat.enable_timing(True)
+        r = lat.fix(Um, 0.08, 1e-15, "mixed", theta_switch=1e-8)
+        names = set(lat.kernel_times())
+        r64 = lat.fix(U.copy(), 0.08, 1e-15, "fp64")
+    assert "gauge_update.f64" in names and "update_residual.f32" not in names, names
+    assert "gauge_update_fused_reunit.f32" in names
+    assert r["converged"] and r["theta"] < 1e-15
+    assert abs(r["F"] - r64["F"]) < 1e-12
+    assert abs(r["iters"] - r64["iters"]) <= 3, (r["iters"], r64["iters"])
+    assert oracle.theta(oracle.delta(Um)) < 1e-15
+    assert abs(oracle.functional(Um) - r["F"]) < 1e-12
+    assert abs(oracle.plaquette(Um) - oracle.plaquette(U)) < 1e-14
+
+
 def test_fp32_precision_fix_reaches_float_floor(lgf):
     dims = (8, 8, 8, 8)
     U = synth.config(dims, 1, 0.3)
