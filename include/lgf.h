@@ -213,17 +213,24 @@ lgf_status lgf_batch_describe(const lgf_batch *b, char *buf, int len);
  * allocate. It needs no context: every input and output is the caller's, and the only scratch (per-block
  * partial sums of the reduction and a counter, 1 MiB) is a fixed array inside the library's device
  * image. The call allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
- *   links     device pointer, the links layout above, 16-byte aligned
- *   delta     device pointer to V*9 complex doubles (site-field layout) for Delta(x), or NULL
- *   theta_F   device pointer to 2 doubles: theta (Eq. 4) and F (Eq. 1 at g = 1)
+ *   links     device pointer of the current device, the links layout above, 16-byte aligned
+ *   delta     device pointer of the current device to V*9 complex doubles (site-field layout), 16-byte
+ *             aligned, that receives the gauge-fixing violation Delta(x) of every site; or NULL
+ *   theta_F   device pointer of the current device to 2 doubles, 8-byte aligned: the gauge-fixing
+ *             residual theta (the lattice average of Tr Delta Delta^+ / 3) and the functional F (the
+ *             average of Re Tr U_mu(x) / 3 over sites and directions, i.e. at g = 1)
  *   stream    cudaStream_t to issue on (NULL = the legacy default stream); the call does not wait:
  *             the outputs are complete when the stream reaches that point
  * Limits: V = Nx*Ny*Nz*Nt <= 16777216 (2^24, e.g. 64^4); extents as for lgf_create. Larger lattices,
- * host pointers or bad extents return LGF_EINVAL with a message from lgf_last_error(NULL).
+ * host pointers, pointers of another GPU, misaligned pointers or bad extents return LGF_EINVAL with a
+ * message from lgf_last_error(NULL).
  * The first call on a device looks up the device address of the scratch array (once per device, with
- * that device current); make that first call before any stream capture. All calls on a device share
- * the scratch array, which keeps the last call's contents (the counter is cleared by each call): calls
- * that overlap on the GPU race and give wrong results, so order them on one stream. */
+ * that device current); make that first call before any stream capture. Under CUDA's lazy module
+ * loading, that first call (or the first launch) is also when the device commits memory for the 1 MiB
+ * array, so it can fail with LGF_ECUDA if the device is full at that moment: make the first call, as a
+ * warm-up, while device memory is still available. All calls on a device share the scratch array, which
+ * keeps the last call's contents (the counter is cleared by each call): calls that overlap on the GPU
+ * race and give wrong results, so order them on one stream. */
 lgf_status lgf_delta_noalloc(const double *links, int Nx, int Ny, int Nz, int Nt, double *delta, double *theta_F,
                              void *stream);
 

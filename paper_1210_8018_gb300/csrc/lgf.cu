@@ -514,13 +514,20 @@ lgf_status ensure_staging(lgf_ctx *ctx, double **buf, size_t *have, size_t bytes
   return LGF_OK;
 }
 
-bool is_device_ptr(const void *p) {
+enum PtrKind { PTR_HOST = 0, PTR_DEVICE = 1, PTR_OTHER_DEVICE = 2 };
+
+// Host memory (pageable, or page-locked), memory the kernels of the context's device can use directly
+// (device memory of that device, or managed memory), or device memory of another GPU (rejected: the
+// kernels would reach it only through peer access, which the library does not enable).
+PtrKind ptr_kind(const void *p, int device) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return PTR_HOST;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return PTR_DEVICE;
+  if (a.type == cudaMemoryTypeDevice) return a.device == device ? PTR_DEVICE : PTR_OTHER_DEVICE;
+  return PTR_HOST;
 }
 
 // Resolve a caller buffer of `bytes` to a device pointer: device memory as it is, host memory staged
@@ -528,7 +535,9 @@ bool is_device_ptr(const void *p) {
 // the host link).
 lgf_status input_ptr(lgf_ctx *ctx, const double *p, size_t bytes, double **buf, size_t *have, const double **out) {
   if (!p) return fail(ctx, LGF_EINVAL, "null buffer");
-  if (is_device_ptr(p)) {
+  const PtrKind k = ptr_kind(p, ctx->device);
+  if (k == PTR_OTHER_DEVICE) return fail(ctx, LGF_EINVAL, "device buffer belongs to another GPU than the context's");
+  if (k == PTR_DEVICE) {
     if (((uintptr_t)p) & 15) return fail(ctx, LGF_EINVAL, "device buffers must be 16-byte aligned");
     *out = p;
     return LGF_OK;
@@ -541,7 +550,9 @@ lgf_status input_ptr(lgf_ctx *ctx, const double *p, size_t bytes, double **buf, 
 
 lgf_status output_ptr(lgf_ctx *ctx, double *p, size_t bytes, double **buf, size_t *have, double **dev, bool *host) {
   if (!p) return fail(ctx, LGF_EINVAL, "null buffer");
-  if (is_device_ptr(p)) {
+  const PtrKind k = ptr_kind(p, ctx->device);
+  if (k == PTR_OTHER_DEVICE) return fail(ctx, LGF_EINVAL, "device buffer belongs to another GPU than the context's");
+  if (k == PTR_DEVICE) {
     if (((uintptr_t)p) & 15) return fail(ctx, LGF_EINVAL, "device buffers must be 16-byte aligned");
     *dev = p;
     *host = false;
@@ -895,6 +906,7 @@ static lgf_status create_ctx(const int n[4], int nb, lgf_ctx **out) {
   }
   auto bail = [&](lgf_status s, const std::string &m) {
     g_last_static_error = m;
+    g_static_literal = nullptr;
     delete ctx;
     return s;
   };
@@ -935,6 +947,7 @@ static lgf_status create_ctx(const int n[4], int nb, lgf_ctx **out) {
         cudaMemcpy(ctx->p2part[mu], part.data(), sizeof(double) * n[mu], cudaMemcpyHostToDevice) != cudaSuccess) {
       lgf_destroy(ctx);
       g_last_static_error = "allocation of FFT tables failed";
+      g_static_literal = nullptr;
       return LGF_ENOMEM;
     }
   }

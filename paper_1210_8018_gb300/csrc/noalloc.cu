@@ -145,13 +145,17 @@ __global__ void __launch_bounds__(kNoAllocThreads)
   }
 }
 
-bool on_device(const void *p) {
+// Memory the kernel can use directly on device `dev`: device memory of that device, or managed memory.
+// Device memory of another GPU is refused: the kernel would reach it only through peer access, which this
+// library never enables.
+bool on_device(const void *p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 bool extent_ok(int n) {
@@ -177,18 +181,19 @@ extern "C" lgf_status lgf_delta_noalloc(const double *links, int Nx, int Ny, int
     lgf_set_static_error("lattice volume exceeds the 16777216-site limit of the fixed scratch array");
     return LGF_EINVAL;
   }
-  if (!links || !theta_F || !on_device(links) || !on_device(theta_F) || (delta && !on_device(delta))) {
-    lgf_set_static_error("links, delta and theta_F must be device pointers (theta_F and links not NULL)");
-    return LGF_EINVAL;
-  }
-  if ((((uintptr_t)links) | ((uintptr_t)delta)) & 15) {
-    lgf_set_static_error("links and delta must be 16-byte aligned");
-    return LGF_EINVAL;
-  }
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
     lgf_set_static_error("no usable current CUDA device");
     return LGF_ECUDA;
+  }
+  if (!links || !theta_F || !on_device(links, dev) || !on_device(theta_F, dev) || (delta && !on_device(delta, dev))) {
+    lgf_set_static_error("links, delta and theta_F must be device pointers of the current device "
+                         "(theta_F and links not NULL)");
+    return LGF_EINVAL;
+  }
+  if (((((uintptr_t)links) | ((uintptr_t)delta)) & 15) || (((uintptr_t)theta_F) & 7)) {
+    lgf_set_static_error("links and delta must be 16-byte aligned, theta_F 8-byte aligned");
+    return LGF_EINVAL;
   }
   NoAllocScratch *scratch = nullptr;
   {

@@ -73,3 +73,22 @@ def test_no_oracle_in_product_path():
         if os.path.isfile(path) and path.endswith((".py", ".cu", ".cuh", ".h")):
             src = open(path).read()
             assert "import oracle" not in src and "oracle." not in src and "liboracle" not in src, path
+
+
+def test_noalloc_message_does_not_outlive_a_later_failure(lib):
+    """A rejected lgf_delta_noalloc call sets the context-free error message; a later failing lgf_create
+    must replace it with its own message (checked on a machine without a GPU, where lgf_create fails when
+    it asks for the device)."""
+    lib.lgf_create.argtypes = [ctypes.c_int] * 4 + [ctypes.POINTER(ctypes.c_void_p)]
+    lib.lgf_last_error.restype = ctypes.c_char_p
+    lib.lgf_delta_noalloc.argtypes = [ctypes.c_void_p] + [ctypes.c_int] * 4 + [ctypes.c_void_p] * 3
+    assert lib.lgf_delta_noalloc(None, 7, 4, 4, 4, None, None, None) == 1  # LGF_EINVAL before any CUDA call
+    assert b"products of 2, 3 and 5" in lib.lgf_last_error(None)
+    h = ctypes.c_void_p()
+    st = lib.lgf_create(4, 4, 4, 4, ctypes.byref(h))
+    if st == 0:
+        lib.lgf_destroy.argtypes = [ctypes.c_void_p]
+        lib.lgf_destroy(h)
+        pytest.skip("a CUDA device is present: lgf_create does not fail here")
+    assert st == 3  # LGF_ECUDA: no device
+    assert b"products of 2, 3 and 5" not in lib.lgf_last_error(None)
