@@ -161,6 +161,14 @@ lgf_status lgf_gauge(lgf_ctx *ctx, const double *dtilde, double alpha, double *g
 /* Algorithm 1: U_mu(x) -> g(x) U_mu(x) g^+(x + mu) for all x, mu (links in/out, g in). */
 lgf_status lgf_update(lgf_ctx *ctx, double *links, const double *g, int precision);
 
+/* Algorithm 1, FFT block, on an su(3) coefficient field: out[8*s + a] = F^-1[(p^2_max/p^2) F[c^a]](s) / V
+ * for each of the eight real fields c^a(s) = coef[8*s + a] (zero mode set to 0). The filter is real and
+ * even in k, so each real field stays real, and filtering the coefficients equals filtering the matrix
+ * field sum_a c^a M^a element by element for any constant basis M^a (e.g. i T^a). It preconditions the
+ * su(3) gradient of lgf_functional_grad the way Algorithm 1 preconditions Delta. coef and out: V*8
+ * doubles, site-major, device (16-byte aligned) or host pointers; they may be the same buffer. */
+lgf_status lgf_filter_coeffs(lgf_ctx *ctx, const double *coef, double *out, int precision);
+
 /* ---- The functional as a differentiable function of a Lie-algebra field (Eq. 1 at g = exp(i omega)).
  * omega: V*8 doubles, site-major: omega[8*s + a] is the coefficient of T^a = lambda^a/2 (Gell-Mann
  * matrices), so omega(x) = sum_a omega^a T^a is Hermitian and traceless; g(x) = exp(i omega(x)) is

@@ -48,6 +48,7 @@ _SIGS = {
     "lgf_store": (_i, [_vp, _vp]),
     "lgf_delta": (_i, [_vp, _vp, _vp, _P(_d), _P(_d), _i]),
     "lgf_filter": (_i, [_vp, _vp, _vp, _i]),
+    "lgf_filter_coeffs": (_i, [_vp, _vp, _vp, _i]),
     "lgf_gauge": (_i, [_vp, _vp, _d, _vp, _i]),
     "lgf_update": (_i, [_vp, _vp, _vp, _i]),
     "lgf_functional": (_i, [_vp, _vp, _vp, _P(_d), _vp]),
@@ -226,6 +227,12 @@ class Lattice:
         self._bind(delta, out)
         self._check(_lib.lgf_filter(self._h, _ptr(delta), _ptr(out), _PREC[precision]))
 
+    def filter_coeffs(self, coef, out, precision="fp64"):
+        """The p^2_max/p^2 filter of Algorithm 1 on each of the eight real fields coef[:, a] (float64,
+        (V, 8) or (Nt, Nz, Ny, Nx, 8)); out may be coef itself."""
+        self._bind(coef, out)
+        self._check(_lib.lgf_filter_coeffs(self._h, _ptr(coef, True), _ptr(out, True), _PREC[precision]))
+
     def gauge(self, dtilde, alpha, out, precision="fp64"):
         self._bind(dtilde, out)
         self._check(_lib.lgf_gauge(self._h, _ptr(dtilde), float(alpha), _ptr(out), _PREC[precision]))
@@ -355,59 +362,45 @@ def LandauF():
     return _LandauF
 
 
-def _gell_mann_basis(device):
-    import torch
-    l = torch.zeros((8, 3, 3), dtype=torch.complex128)
-    l[0, 0, 1] = l[0, 1, 0] = 1
-    l[1, 0, 1], l[1, 1, 0] = -1j, 1j
-    l[2, 0, 0], l[2, 1, 1] = 1, -1
-    l[3, 0, 2] = l[3, 2, 0] = 1
-    l[4, 0, 2], l[4, 2, 0] = -1j, 1j
-    l[5, 1, 2] = l[5, 2, 1] = 1
-    l[6, 1, 2], l[6, 2, 1] = -1j, 1j
-    l[7] = torch.diag(torch.tensor([1, 1, -2], dtype=torch.complex128)) / 3 ** 0.5
-    return l.to(device)
-
-
-def _fourier_precondition(lat, grad, basis, dims):
-    """Apply the p^2_max/p^2 filter of Algorithm 1 to a gradient field (V x 8 coefficients of lambda^a)
-    with the library's FFT kernels: the field is written as the anti-Hermitian traceless matrices
-    i sum_a grad^a lambda^a, filtered element by element, and projected back."""
-    import torch
-    nx, ny, nz, nt = dims
-    M = 1j * torch.einsum("sa,aij->sij", grad.to(torch.complex128), basis)
-    M = M.reshape(nt, nz, ny, nx, 3, 3).contiguous()
-    out = torch.empty_like(M)
-    lat.filter(M, out)
-    # coefficient of i lambda^a: Tr(lambda^a (-i M)) / 2
-    return 0.5 * torch.einsum("aij,sji->sa", basis, -1j * out.reshape(-1, 3, 3)).real.contiguous()
-
-
-def adam_fix(U, target=1e-10, lr=1e-2, max_steps=20000, check_every=20, lr_decay=0.5, min_lr=1e-9,
-             omega0=None, precondition=False, optimizer="adam", rebase_every=0):
+def adam_fix(U, target=1e-10, lr=1e-2, max_steps=20000, check_every=20, lr_decay=0.5, min_lr=1e-12,
+             omega0=None, precondition=False, optimizer="adam", rebase_every=0, keep_moments=True,
+             betas=(0.9, 0.999), amsgrad=False, adam_eps=1e-8, patience=0):
     """Maximise F_U[exp(i omega)] over omega with a torch optimiser, using the library's forward and
     backward kernels, until theta of the transformed links g U g^+ falls to `target`.
 
-    optimizer="adam": torch.optim.Adam on the plain gradient (no Fourier acceleration). omega starts at
-    omega0 (default 0); every `check_every` steps F and theta are evaluated, and the learning rate is
-    multiplied by `lr_decay` whenever F did not increase since the previous check.
-    optimizer="sgd": torch.optim.SGD. With precondition=True the gradient first passes through the
-    p^2_max/p^2 filter of Algorithm 1 (the library's FFT kernels); lr = 24 alpha V with re-basing after
-    every step (rebase_every=1: g is absorbed into U and omega reset to 0) reproduces the step of
-    Algorithm 1 with the exponential in place of its first-order expansion.
-    Re-basing applies g to U exactly (FP64, lgf_update) and starts a new optimiser (moments refer to the
-    old coordinates). At the end g is applied to U in place. Returns dict(theta, F, F0, steps, lr,
-    history=[(step, theta, F, lr)])."""
+    The optimiser minimises the loss -24 V F (V sites): its gradient with respect to omega^a(x) at omega = 0
+    is i Tr[T^a Delta(x)], of the size of Delta itself, so Adam's epsilon stays negligible down to small
+    theta. omega starts at omega0 (default 0). Every `check_every` steps F and theta are evaluated, and the
+    learning rate is multiplied by `lr_decay` once F has not risen above its best value for more than
+    `patience` consecutive checks (patience = 0: whenever F did not increase). A momentum method such as
+    Adam does not raise F at every step even when it converges, so with frequent checks give it some
+    patience.
+
+    optimizer="adam": torch.optim.Adam (betas, amsgrad and adam_eps are passed through); "sgd":
+    torch.optim.SGD. With precondition=True the gradient first passes through the p^2_max/p^2 filter of
+    Algorithm 1 (lgf_filter_coeffs, the library's FFT kernels), which removes the critical slowing down of
+    the plain gradient. SGD with lr = alpha on the preconditioned gradient and re-basing after every step
+    is the step of Algorithm 1 with the exponential in place of its first-order expansion.
+
+    Re-basing (every `rebase_every` steps, 0 = never) applies g = exp(i omega) to U exactly (FP64,
+    lgf_update) and resets omega to 0, so the gradient is always taken near omega = 0, where its
+    coordinates are those of the Lie algebra at the current links. With keep_moments=True the optimiser's
+    state (Adam's first and second moments) is carried over unchanged: both coordinate systems are the Lie
+    algebra at nearby points, identified by left translation, and they differ by O(|omega|) per component
+    (|omega| is one step). With keep_moments=False a new optimiser starts after each re-basing.
+    At the end g is applied to U in place. Returns dict(theta, F, F0, steps, lr, history=[(step, theta, F,
+    lr)])."""
     import torch
     dims = dims_of(U)
     V = int(np.prod(dims))
     LF = LandauF()
     hist = []
+    scale = 24.0 * V
 
     def make_opt(rate):
         if optimizer == "sgd":
             return torch.optim.SGD([omega], lr=rate)
-        return torch.optim.Adam([omega], lr=rate)
+        return torch.optim.Adam([omega], lr=rate, betas=betas, amsgrad=amsgrad, eps=adam_eps)
 
     with Lattice(dims) as lat:
         omega = torch.zeros((V, 8), dtype=torch.float64, device=U.device) if omega0 is None else omega0.clone()
@@ -426,30 +419,35 @@ def adam_fix(U, target=1e-10, lr=1e-2, max_steps=20000, check_every=20, lr_decay
         F, theta = evaluate()
         hist.append((0, theta, F, lr))
         opt = make_opt(lr)
-        basis = _gell_mann_basis(U.device) if precondition else None
         step = 0
+        best, stale = F, 0
         while step < max_steps and theta > target and opt.param_groups[0]["lr"] > min_lr:
             opt.zero_grad(set_to_none=False)
-            loss = -LF.apply(omega, U, lat)
+            loss = -scale * LF.apply(omega, U, lat)
             loss.backward()
             if precondition:
                 with torch.no_grad():
-                    omega.grad.copy_(_fourier_precondition(lat, omega.grad, basis, dims))
+                    lat.filter_coeffs(omega.grad, omega.grad)
             opt.step()
             step += 1
             rebase = rebase_every > 0 and step % rebase_every == 0
             if step % check_every == 0 or rebase:
-                F_prev = F
                 F, theta = evaluate()
-                if F <= F_prev and optimizer == "adam":
-                    for pg in opt.param_groups:
-                        pg["lr"] *= lr_decay
+                if F > best:
+                    best, stale = F, 0
+                else:
+                    stale += 1
+                    if stale > patience:
+                        for pg in opt.param_groups:
+                            pg["lr"] *= lr_decay
+                        stale = 0
                 hist.append((step, theta, F, opt.param_groups[0]["lr"]))
                 if rebase:
                     U.copy_(Ut)
                     with torch.no_grad():
                         omega.zero_()
-                    opt = make_opt(opt.param_groups[0]["lr"])
+                    if not keep_moments:
+                        opt = make_opt(opt.param_groups[0]["lr"])
         F, theta = evaluate()
         U.copy_(Ut)
     return dict(theta=theta, F=F, F0=F0, steps=step, lr=opt.param_groups[0]["lr"], history=hist)

@@ -1216,20 +1216,15 @@ lgf_status lgf_measure(lgf_ctx *ctx, const double *links, double *theta, double 
   memset(&ctx->ctrl_host, 0, sizeof(Ctrl));
   TRY(write_ctrl(ctx));
   TRY(launch_delta<double>(ctx, ctx->s64, 0, 0));
+  if (plaq) {
+    // stream-ordered after the Delta reduction, which leaves the last-block counter at zero
+    k_plaquette<double, NT><<<ctx->nblocks_site, NT, 0, ctx->stream>>>(ctx->s64.U, ctx->partials, ctx->ctrl, ctx->L);
+    CKL();
+  }
   TRY(read_ctrl(ctx));
   if (theta) *theta = ctx->ctrl_host.theta;
   if (F) *F = ctx->ctrl_host.F;
-  if (plaq) {
-    k_plaquette<double, NT><<<ctx->nblocks_site, NT, 0, ctx->stream>>>(ctx->s64.U, ctx->partials, ctx->L);
-    CKL();
-    std::vector<double> part(ctx->nblocks_site);
-    CK(cudaMemcpyAsync(part.data(), ctx->partials, sizeof(double) * ctx->nblocks_site, cudaMemcpyDeviceToHost,
-                       ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-    double s = 0;
-    for (double v : part) s += v;
-    *plaq = s / (3.0 * 6.0 * (double)V);
-  }
+  if (plaq) *plaq = ctx->ctrl_host.plaq;
   ctx->loaded = false;  // the working links were overwritten
   return LGF_OK;
 }
@@ -1326,6 +1321,45 @@ extern "C" lgf_status lgf_filter(lgf_ctx *ctx, const double *delta, double *dtil
     TRY(step_filter<double>(ctx, ctx->s64, src, dst));
   }
   if (host) CK(cudaMemcpyAsync(dtilde, dst, (size_t)V * 144, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->loaded = false;
+  return LGF_OK;
+}
+
+template <typename T>
+static lgf_status step_filter_coeffs(lgf_ctx *ctx, State<T> &S, const double *src, double *dst) {
+  TRY(with_fft_type<T>(ctx, [&](auto tag) -> lgf_status {
+    using FT = decltype(tag);
+    k_pack_coeffs<FT><<<grid1(ctx->V, NT), NT, 0, ctx->stream>>>(src, reinterpret_cast<FT *>(S.P), ctx->V);
+    CKL();
+    return LGF_OK;
+  }));
+  TRY(launch_filter<T>(ctx, S, S.P, 0));
+  return with_fft_type<T>(ctx, [&](auto tag) -> lgf_status {
+    using FT = decltype(tag);
+    k_unpack_coeffs<FT><<<grid1(ctx->V, NT), NT, 0, ctx->stream>>>(reinterpret_cast<const FT *>(S.P), dst, ctx->V);
+    CKL();
+    return LGF_OK;
+  });
+}
+
+extern "C" lgf_status lgf_filter_coeffs(lgf_ctx *ctx, const double *coef, double *out, int precision) {
+  TRY(check_ctx(ctx));
+  TRY(ensure_common(ctx));
+  const int64_t V = ctx->V;
+  const double *src = nullptr;
+  TRY(input_ptr(ctx, coef, (size_t)V * 64, &ctx->staging, &ctx->staging_bytes, &src));
+  double *dst = nullptr;
+  bool host = false;
+  TRY(output_ptr(ctx, out, (size_t)V * 64, &ctx->staging2, &ctx->staging2_bytes, &dst, &host));
+  if (precision == LGF_FP32) {
+    TRY(setup_precision<float>(ctx, ctx->s32));
+    TRY(step_filter_coeffs<float>(ctx, ctx->s32, src, dst));
+  } else {
+    TRY(setup_precision<double>(ctx, ctx->s64));
+    TRY(step_filter_coeffs<double>(ctx, ctx->s64, src, dst));
+  }
+  if (host) CK(cudaMemcpyAsync(out, dst, (size_t)V * 64, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->loaded = false;
   return LGF_OK;

@@ -42,6 +42,7 @@ struct Ctrl {
   int stage;             // precision of the live links: 0 float, 1 double, 2 the residual stage of the
                          // mixed schedule; kernels of another stage return at once (a batch launches
                          // the float and the double kernels in the mixed schedule)
+  double plaq;           // average plaquette, written by k_plaquette
 };
 constexpr int kStageResidual = 2;
 
@@ -759,9 +760,35 @@ template <typename PT> __global__ void k_unpack_antiherm(const PT *__restrict__ 
   for (int e = 0; e < 9; ++e) dst[e] = make_double2((double)m.e[e].r, (double)m.e[e].i);
 }
 
+// The eight real coefficient fields of an su(3) field, c^a(s) = coef[8 s + a], held as the four complex
+// fields c^(2j) + i c^(2j+1), j = 0..3, in the packed planes: the Fourier filter of Algorithm 1 is real and
+// even in k, so it maps the real and the imaginary part of each plane separately, and the planes come back
+// as the four pairs of filtered coefficient fields.
+template <typename PT> __global__ void k_pack_coeffs(const double *__restrict__ c, PT *__restrict__ P, int64_t V) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  const double2 *q = reinterpret_cast<const double2 *>(c) + s * 4;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const double2 v = q[j];
+    st(P, (int64_t)j * V + s, mkc(convert<PT>(v.x), convert<PT>(v.y)));
+  }
+}
+
+template <typename PT> __global__ void k_unpack_coeffs(const PT *__restrict__ P, double *__restrict__ c, int64_t V) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  double2 *q = reinterpret_cast<double2 *>(c) + s * 4;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const cx<PT> v = ldg(P, (int64_t)j * V + s);
+    q[j] = make_double2(convert<double>(v.r), convert<double>(v.i));
+  }
+}
+
 // Average plaquette partials: (1/3) Re Tr U_mu(x) U_nu(x+mu) U_mu^+(x+nu) U_nu^+(x) over mu < nu.
 template <typename T, int NT>
-__global__ void __launch_bounds__(NT) k_plaquette(const T *__restrict__ U, double *partials, Lattice L) {
+__global__ void __launch_bounds__(NT) k_plaquette(const T *__restrict__ U, double *partials, Ctrl *ctrl, Lattice L) {
   const int64_t V = L.V;
   double acc = 0.0;
   for (int k = 0; k < kSitesPerThread; ++k) {
@@ -787,9 +814,26 @@ __global__ void __launch_bounds__(NT) k_plaquette(const T *__restrict__ U, doubl
         for (int e = 0; e < 9; ++e) acc += (double)t.e[e].r * w.e[e].r + (double)t.e[e].i * w.e[e].i;
       }
   }
+  // block sums, then the last block to finish sums the partials in block order (as for theta and F)
+  __shared__ bool last;
   double dummy = 0.0;
   block_sum2<NT>(acc, dummy);
-  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = acc;
+    __threadfence();
+    last = (atomicAdd(&ctrl->ticket, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double a = 0.0, b = 0.0;
+  for (unsigned k = threadIdx.x; k < gridDim.x; k += NT) a += __ldcg(partials + k);
+  __syncthreads();
+  block_sum2<NT>(a, b);
+  if (threadIdx.x == 0) {
+    ctrl->plaq = a / (3.0 * 6.0 * (double)V);  // (1/3) Re Tr over V sites and 6 planes
+    ctrl->ticket = 0;
+  }
 }
 
 }  // namespace lgf
