@@ -233,20 +233,105 @@ def run_reference(args, dims, rank, ws):
     print(json.dumps(line), flush=True)
 
 
+def schedule_of(args):
+    """What the headline schedule does, stage by stage."""
+    if args.precision == "fp64":
+        return {"stages": "double path: FP64 links and sums (exact fixed-point Delta, double-float filter and "
+                          "small-step forms at FP64 rounding level) to theta < 1e-15"}
+    if args.precision == "fp32":
+        return {"stages": "float links, FFTs and updates with FP64 reductions throughout"}
+    return {"float_stage": "float links (rows 0-1), FFTs and updates; theta and F sums in FP64",
+            "handover": "theta <= %g (or when a chunk of float iterations stops lowering theta)" % args.theta_switch,
+            "reprojection": "float links and accumulated transformation G projected onto SU(3) in float every 16 "
+                            "float iterations",
+            "handover_links": "U = G U0 G^+(x+mu) from the saved FP64 input, in 61-bit fixed point (exact to FP64 "
+                              "rounding)",
+            "final_approach": "float iterations on the residual R of U = U_h + R, then the double links rebuilt "
+                              "exactly by the double update; theta < 1e-15 checked in FP64"}
+
+
 def config_of(args, dims, path):
     return {"workload": "%s SU(3) lattice, U=h exp(i eps A) h^+(x+mu), eps=%g, seed %d; alpha=0.08, "
                         "theta<1e-15; %s" % ("^".join(["64", "4"]) if dims == (64, 64, 64, 64) else "x".join(map(str, dims)),
                                              args.eps, args.seed, path),
             "lattice": list(dims), "precision": args.precision, "theta_switch": args.theta_switch,
+            "schedule": schedule_of(args),
             "step": "one complete gauge fixing (Algorithm 1 until theta < 1e-15)",
             "l2": ("no flush: links %.3g GB per step >> 129 MB L2" % (int(np.prod(dims)) * 576 / 1e9)
                    if np.prod(dims) >= 2 ** 20 else "small lattice"),
             "parallelism": "replicas"}
 
 
-def cpu_baseline(dims, args, V_gpu):
+def load_golden(dims, seed, eps):
+    """The FP64 oracle's complete fix of this configuration, stored in tests/golden/ by a script that calls
+    only the oracle (None when no stored fix matches)."""
+    path = os.path.join(ROOT, "tests", "golden", "oracle_fix_%s_s%d.json" % ("x".join(map(str, dims)), seed))
+    if not os.path.exists(path):
+        return None
+    g = json.load(open(path))
+    if tuple(g["dims"]) != tuple(dims) or g["seed"] != seed or abs(g["eps"] - eps) > 1e-12:
+        return None
+    return g
+
+
+def error_vs_oracle(res, golden):
+    """Errors of one schedule's result against the oracle's fix of the same configuration: F (both are the
+    same maximum, relative), the plaquette (gauge invariant: the fixed links against the input), theta (both
+    final values are below 1e-15; reported side by side), the iteration count and, for the double path, the
+    largest per-iteration deviation of theta and F along the whole trajectory."""
+    if golden is None:
+        return None
+    out = {"reference": "FP64 CPU oracle, complete fix of the same configuration (%d iterations)" % golden["iters"],
+           "F_rel_err": abs(res["F"] - golden["F"]) / abs(golden["F"]),
+           "plaquette_err_vs_input": abs(res["plaquette"] - golden["plaquette_in"]),
+           "plaquette_err_vs_oracle_output": abs(res["plaquette"] - golden["plaquette_out"]),
+           "theta": res["theta"], "theta_oracle": golden["theta"],
+           "iters": res["iters"], "iters_oracle": golden["iters"]}
+    if "history" in res:
+        h, ho = np.asarray(res["history"]), np.asarray(golden["history"])
+        n = min(len(h), len(ho))
+        out["history_theta_max_rel_err"] = float(np.max(np.abs(h[:n, 0] - ho[:n, 0]) / ho[:n, 0]))
+        out["history_F_max_rel_err"] = float(np.max(np.abs(h[:n, 1] - ho[:n, 1]) / np.abs(ho[:n, 1])))
+    return out
+
+
+def spec_lattice(lgf, dims):
+    """A context whose float stage reprojects in double and which runs double iterations after the handover
+    (the switches are read when the context is created)."""
+    saved = {k: os.environ.get(k) for k in ("LGF_REUNIT_FP64", "LGF_RESIDUAL")}
+    os.environ["LGF_REUNIT_FP64"], os.environ["LGF_RESIDUAL"] = "1", "0"
+    try:
+        return lgf.Lattice(dims)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
+def kernel_table(ktimes, dims, hbm, alu_peak):
+    """Per kernel: launches, time, share, and achieved algorithmic GB/s (and ALU rate) against the peaks."""
+    kernels = {}
+    total_ms = sum(v[1] for v in ktimes.values()) or 1.0
+    for name, (n, kms) in ktimes.items():
+        b, f, kind = algorithmic(name, dims)
+        per = kms / max(n, 1) / 1e3
+        gbs = b / per / 1e9 if per > 0 else 0.0
+        d = {"launches": n, "ms_total": round(kms, 3), "share": round(kms / total_ms, 4),
+             "ms_per_launch": round(kms / max(n, 1), 4), "GB_s": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4)}
+        if kind and per > 0:
+            d["alu_kind"] = kind
+            d["alu_frac"] = round(f / per / alu_peak[kind][0], 4)
+        kernels[name] = d
+    return kernels
+
+
+def cpu_baseline(dims, args, V_gpu, golden=None, gpu_iters=None):
     """The oracle as it stands on the host cores, on a bounded sample: one iteration of Algorithm 1 on
-    the same configuration (falls back to a 32^4 configuration when host memory is short)."""
+    the same configuration (falls back to a 32^4 configuration when host memory is short). The time to
+    theta < 1e-15 is extrapolated: the per-iteration time times the oracle's own iteration count on this
+    configuration (stored by the oracle's complete fix), or else the GPU's."""
     import oracle
     import synth
     need = int(np.prod(dims)) * 4 * 144 * 3.2
@@ -263,9 +348,17 @@ def cpu_baseline(dims, args, V_gpu):
     t0 = time.perf_counter()
     oracle.fix(U, 0.08, 0.0, 1)
     dt = time.perf_counter() - t0
-    return {"value": Vc / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "one iteration of Algorithm 1 (plus the initial Delta/theta/F) on the %s configuration, "
-                      "%.1f s" % ("x".join(map(str, cdims)), dt)}
+    out = {"value": Vc / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+           "sample": "one iteration of Algorithm 1 (plus the initial Delta/theta/F) on the %s configuration, "
+                     "%.1f s" % ("x".join(map(str, cdims)), dt)}
+    n_it = golden["iters"] if golden else gpu_iters
+    if n_it:
+        out["time_to_theta_extrapolated_s"] = dt * (V_gpu / Vc) * n_it
+        out["time_to_theta_note"] = ("extrapolated: per-iteration time x %d iterations (%s)%s"
+                                     % (n_it, "the oracle's own count on this configuration" if golden
+                                        else "the GPU's count", "" if cdims == dims else
+                                        " x the volume ratio %d/%d" % (V_gpu, Vc)))
+    return out
 
 
 def _timed(torch, fn):
@@ -279,7 +372,9 @@ def _timed(torch, fn):
 def run_batch(args):
     """The batched ensemble: 48 configurations (16 each of 16^4, 24^3x48, 32^3x64), eps_i ~ U[0.4, 0.7]
     (seed 99), configuration i from seed 100 + i; fixed together in FP64 and in the mixed schedule
-    (grouped launches, CUDA-graph replay, autotuned FFT passes). Links stay on the device."""
+    (grouped launches, CUDA-graph replay, autotuned FFT passes). Links stay on the device. Each schedule:
+    W untimed fixes of the whole ensemble (the first also tunes the FFT passes on a cold cache), then K
+    timed fixes; the copy of the inputs into the working buffers precedes each fix, outside its timing."""
     import torch
     import paper_1210_8018_gb300 as lgf
     import synth
@@ -293,19 +388,29 @@ def run_batch(args):
     sites = sum(int(np.prod(d)) for d in shapes)
     out = {"metric": "site-iterations/s, batched ensemble of uneven lattices", "unit": UNIT,
            "config": {"workload": "16 x 16^4 + 16 x 24^3x48 + 16 x 32^3x64, eps ~ U[0.4,0.7], alpha=0.08, theta<1e-15",
-                      "sites": sites}, "data": "synthetic"}
+                      "sites": sites, "l2": "no flush: 26 GB of links per fix >> 129 MB L2"},
+           "data": "synthetic", "steps": args.steps, "warmup": args.warmup}
     with lgf.Batch(shapes) as b:
         for prec in ("mixed", "fp64"):
             def run():
                 for w, u in zip(work, inputs):
                     w.copy_(u)
                 torch.cuda.synchronize()
-                return b.fix(work, 0.08, 1e-15, prec)
-            run()  # warm-up (and autotuning on a cold cache)
-            res, dt = _timed(torch, run)
+                t0 = time.perf_counter()
+                res = b.fix(work, 0.08, 1e-15, prec)
+                torch.cuda.synchronize()
+                return res, time.perf_counter() - t0
+            for _ in range(args.warmup):
+                run()
+            times = []
+            for _ in range(args.steps):
+                res, dt = run()
+                times.append(dt)
+            dt = statistics.median(times)
             its = [r["iters"] for r in res]
             siters = sum(int(np.prod(d)) * r["iters"] for d, r in zip(shapes, res))
-            out[prec] = {"time_to_theta_s": dt, "site_iterations_per_s": siters / dt,
+            out[prec] = {"time_to_theta_s": dt, "samples_s": [round(t, 4) for t in times],
+                         "site_iterations_per_s": siters / dt,
                          "converged": sum(r["status"] == 0 for r in res), "iters_min": min(its),
                          "iters_max": max(its), "describe": b.describe()}
     out["value"] = out["mixed"]["site_iterations_per_s"]
@@ -313,11 +418,15 @@ def run_batch(args):
 
 
 def run_scan(args):
-    """The paper's tuning sweep over 32^3 x n (n = 8, 16, 32, 64): site-iterations/s of complete fixes
-    in FP64 and in the mixed schedule."""
+    """The paper's tuning sweep over 32^3 x n (n = 8, 16, 32, 64): site-iterations/s of complete fixes in FP64
+    and in the mixed schedule (W untimed, then K timed fixes, CUDA events on the working stream), with the
+    per-kernel roofline of each."""
     import torch
     import paper_1210_8018_gb300 as lgf
     import synth
+    hbm, sm_max, which = peaks()
+    clk_hz = sm_max * 1e6
+    alu_peak = {"fp64": (FP64_FLOP_PER_CLK * clk_hz, "TFLOP/s", ""), "fp32": (FP32_OPS_PER_CLK * clk_hz, "Tops/s", "")}
     rows = []
     for n in (8, 16, 32, 64):
         dims = (32, 32, 32, n)
@@ -326,24 +435,46 @@ def run_scan(args):
         W = torch.empty_like(U)
         row = {"lattice": "32^3x%d" % n, "sites": V}
         with lgf.Lattice(dims) as lat:
+            stream = torch.cuda.current_stream()
+            lat.set_stream(stream)
             for prec in ("fp64", "mixed"):
                 def run():
                     lat.load(U, prec)
                     r = lat.iterate(1 << 30, 0.08, 1e-15)
                     lat.store(W)
                     return r
-                run()
-                r, dt = _timed(torch, run)
-                row[prec] = {"iters": r["iters"], "time_s": dt, "site_iterations_per_s": V * r["iters"] / dt}
+                for _ in range(args.warmup):
+                    run()
+                lat.enable_timing(True)
+                lat.kernel_times()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                its = 0
+                for _ in range(args.steps):
+                    r = run()
+                    its += r["iters"]
+                e1.record(stream)
+                torch.cuda.synchronize()
+                kt = lat.kernel_times()
+                lat.enable_timing(False)
+                dt = e0.elapsed_time(e1) / 1e3
+                kern = kernel_table(kt, dims, hbm, alu_peak)
+                dom = max(kern, key=lambda k: kern[k]["ms_total"])
+                row[prec] = {"iters": r["iters"], "time_s": dt / args.steps, "site_iterations_per_s": V * its / dt,
+                             "dominant_kernel": dom, "dominant_hbm_frac": kern[dom]["hbm_frac"],
+                             "kernels": {k: {"share": v["share"], "hbm_frac": v["hbm_frac"]} for k, v in kern.items()}}
         rows.append(row)
-    return {"metric": "site-iterations/s over 32^3 x n", "unit": UNIT, "scan": rows,
-            "value": rows[-1]["mixed"]["site_iterations_per_s"], "data": "synthetic"}
+    return {"metric": "site-iterations/s over 32^3 x n", "unit": UNIT, "scan": rows, "steps": args.steps,
+            "warmup": args.warmup, "value": rows[-1]["mixed"]["site_iterations_per_s"], "data": "synthetic",
+            "peak_source": "%s HBM %g GB/s" % (which, hbm)}
 
 
 def run_autograd(args):
     """F_U[exp(i omega)] on 24^4 (eps = 0.5, seed 5; omega ~ N(0, 0.05^2) per generator, seed 6): forward
-    and backward kernel times, the gradient against the oracle's Delta at omega = 0, and Adam over omega
-    until theta <= 1e-10 (or the step budget)."""
+    and backward kernel times, then torch optimisers over omega until theta <= 1e-10: Adam on the
+    Fourier-preconditioned gradient (re-based every 5 steps, moments carried over), plain Adam (bounded
+    number of steps: it slows down critically), and SGD on the preconditioned gradient (Algorithm 1's step)."""
     import torch
     import paper_1210_8018_gb300 as lgf
     import synth
@@ -363,17 +494,20 @@ def run_autograd(args):
         _, tb = _timed(torch, lambda: [lat.functional_grad(U, om, grad) for _ in range(n)])
     out["forward_ms"] = 1e3 * tf / n
     out["backward_ms"] = 1e3 * tb / n
-    runs = (("adam", dict(optimizer="adam", lr=3e-2, max_steps=args.steps * 6000)),
+    runs = (("adam_fourier_preconditioned",
+             dict(optimizer="adam", lr=0.05, precondition=True, rebase_every=5, check_every=5, patience=2,
+                  max_steps=5000)),
+            ("adam_plain", dict(optimizer="adam", lr=3e-2, check_every=20, max_steps=3000)),
             ("sgd_fourier_preconditioned",
-             dict(optimizer="sgd", precondition=True, lr=24 * 0.08 * V, rebase_every=1, check_every=1,
-                  max_steps=args.steps * 100)))
+             dict(optimizer="sgd", precondition=True, lr=0.08, rebase_every=1, check_every=1, max_steps=500)))
     for name, kw in runs:
         Uc = U.clone()
         res, dt = _timed(torch, lambda: lgf.adam_fix(Uc, target=1e-10, omega0=om, **kw))
         out[name] = {k: v for k, v in res.items() if k != "history"}
         out[name]["time_s"] = dt
+        out[name]["reached_target"] = res["theta"] <= 1e-10
         out[name]["theta_trace"] = [(h[0], h[1]) for h in res["history"][::max(1, len(res["history"]) // 20)]]
-    out["value"] = out["adam"]["theta"]
+    out["value"] = out["adam_fourier_preconditioned"]["theta"]
     return out
 
 
@@ -411,8 +545,10 @@ def main():
     torch.cuda.set_device(local)
     if args.batch or args.scan or args.autograd:
         if rank == 0:
-            print(json.dumps(run_batch(args) if args.batch else run_scan(args) if args.scan else run_autograd(args)),
-                  flush=True)
+            with ClockSampler(local) as clk:
+                out = run_batch(args) if args.batch else run_scan(args) if args.scan else run_autograd(args)
+            out["clocks"] = clk.summary()
+            print(json.dumps(out), flush=True)
         return
     if ws > 1:
         import torch.distributed as dist
@@ -425,14 +561,26 @@ def main():
     synth.config(dims, seed, args.eps, out=host.numpy())
     U_in = host.to("cuda", non_blocking=False)
     U_out = torch.empty_like(U_in)
-    lat = lgf.Lattice(dims)
     stream = torch.cuda.current_stream()
-    lat.set_stream(stream)
+    golden = load_golden(dims, seed, args.eps)
 
-    def one_fix(prec):
-        lat.load(U_in, prec)
-        r = lat.iterate(1 << 30, 0.08, 1e-15, theta_switch=args.theta_switch)
-        lat.store(U_out)
+    lat = lgf.Lattice(dims)
+    lat.set_stream(stream)
+    # (name, context, precision, iterate() keywords): the headline schedule first
+    schedules = [(args.precision, lat, args.precision, dict(theta_switch=args.theta_switch))]
+    lat_s = None
+    if args.precision == "mixed" and not args.no_fp64:
+        schedules.append(("fp64", lat, "fp64", {}))
+        lat_s = spec_lattice(lgf, dims)
+        lat_s.set_stream(stream)
+        schedules.append(("mixed_as_specified", lat_s, "mixed", dict(theta_switch=1e-8)))
+    if args.fft32_final and args.precision == "mixed":
+        schedules.append(("mixed_fft32_final", lat, "mixed", dict(theta_switch=args.theta_switch, fft32_final=True)))
+
+    def one_fix(ctx, prec, kw):
+        ctx.load(U_in, prec)
+        r = ctx.iterate(1 << 30, 0.08, 1e-15, **kw)
+        ctx.store(U_out)
         return r
 
     def barrier():
@@ -440,180 +588,120 @@ def main():
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    # warm-up (untimed)
-    for _ in range(args.warmup):
-        r = one_fix(args.precision)
-    lat.enable_timing(True)
-    lat.kernel_times()  # reset counters
-    barrier()
-    iters = []
+    # Every schedule: W untimed warm-up fixes, then K fixes timed with CUDA events on the working stream (one
+    # event pair per fix) inside the clock sampler; then, untimed, the output's plaquette and (double path)
+    # the per-iteration history against the oracle's stored fix of the same configuration.
+    results = {}
     with ClockSampler(local) as clk:
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
-        for _ in range(args.steps):
-            r = one_fix(args.precision)
-            iters.append(r["iters"])
-            if not r["converged"]:
-                raise SystemExit("fix did not converge: %r" % r)
-        ev1.record(stream)
-        barrier()
-    ktimes = lat.kernel_times()
-    ms = ev0.elapsed_time(ev1)
-    t_max, site_iters = reduce_over_ranks(ms, V * sum(iters), ws, "cuda")
-    value = site_iters / (t_max / 1e3)
-    lat.enable_timing(False)
-
-    # plain FP64 on the same field (1 warm-up, 1 timed)
-    fp64 = None
-    if not args.no_fp64 and args.precision != "fp64":
-        one_fix("fp64")
-        barrier()
-        lat.enable_timing(True)
-        lat.kernel_times()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        r64 = one_fix("fp64")
-        e1.record(stream)
-        barrier()
-        k64 = lat.kernel_times()
-        lat.enable_timing(False)
-        t64 = e0.elapsed_time(e1)
-        fp64 = {"time_to_theta_s": t64 / 1e3, "iters": r64["iters"], "site_iterations_per_s": V * r64["iters"] / (t64 / 1e3),
-                "theta": r64["theta"], "F": r64["F"],
-                "kernels_ms": {k: round(v[1], 3) for k, v in sorted(k64.items(), key=lambda kv: -kv[1][1])}}
-
-    # the mixed variant with a float Fourier filter in the double stage (1 warm-up, 1 timed)
-    fast = None
-    if args.fft32_final and args.precision == "mixed":
-        def fix_fast():
-            lat.load(U_in, "mixed")
-            r = lat.iterate(1 << 30, 0.08, 1e-15, theta_switch=args.theta_switch, fft32_final=True)
-            lat.store(U_out)
-            return r
-        fix_fast()
-        barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        rf = fix_fast()
-        e1.record(stream)
-        barrier()
-        tf = e0.elapsed_time(e1)
-        fast = {"time_to_theta_s": tf / 1e3, "iters": rf["iters"], "site_iterations_per_s": V * rf["iters"] / (tf / 1e3),
-                "theta": rf["theta"], "F": rf["F"],
-                "note": "double stage with the Fourier filter in float; links, Delta, g, update and sums in double"}
-
-    # the mixed schedule in its plainest form on the same field (1 warm-up, 1 timed): float links, FFTs and
-    # updates with double reductions and a double-precision reprojection every 16 iterations until
-    # theta <= 1e-8, the handover, and double iterations to theta < 1e-15
-    spec = None
-    if args.precision == "mixed" and not args.no_fp64:
-        saved = {k: os.environ.get(k) for k in ("LGF_REUNIT_FP64", "LGF_RESIDUAL")}
-        os.environ["LGF_REUNIT_FP64"], os.environ["LGF_RESIDUAL"] = "1", "0"
-        try:
-            lat_s = lgf.Lattice(dims)  # the switches are read when the context is created
-        finally:
-            for k, v in saved.items():
-                if v is None:
-                    os.environ.pop(k, None)
-                else:
-                    os.environ[k] = v
-        lat_s.set_stream(stream)
-
-        def fix_spec():
-            lat_s.load(U_in, "mixed")
-            r = lat_s.iterate(1 << 30, 0.08, 1e-15, theta_switch=1e-8)
-            lat_s.store(U_out)
-            return r
-        fix_spec()
-        barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        rs = fix_spec()
-        e1.record(stream)
-        barrier()
-        lat_s.close()
-        ts = e0.elapsed_time(e1)
-        spec = {"time_to_theta_s": ts / 1e3, "iters": rs["iters"], "site_iterations_per_s": V * rs["iters"] / (ts / 1e3),
-                "theta": rs["theta"], "F": rs["F"],
-                "note": "theta_switch 1e-8, float-stage reprojection in double, double iterations after the handover"}
-
-    # roofline of every kernel; the dominant kernel (largest share of the timed steps) is reported
-    hbm, sm_max, which = peaks()
+        for name, ctx, prec, kw in schedules:
+            for _ in range(args.warmup):
+                one_fix(ctx, prec, kw)
+            ctx.enable_timing(True)
+            ctx.kernel_times()  # reset counters
+            barrier()
+            evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+            iters = []
+            evs[0].record(stream)
+            for i in range(args.steps):
+                r = one_fix(ctx, prec, kw)
+                iters.append(r["iters"])
+                evs[i + 1].record(stream)
+                if not r["converged"]:
+                    raise SystemExit("%s fix did not converge: %r" % (name, r))
+            barrier()
+            ktimes = ctx.kernel_times()
+            ctx.enable_timing(False)
+            ms = evs[0].elapsed_time(evs[-1])
+            per = [evs[i].elapsed_time(evs[i + 1]) / 1e3 for i in range(args.steps)]
+            plaq = ctx.measure(U_out)["plaquette"]
+            res = {"time_to_theta_s": ms / args.steps / 1e3, "time_to_theta_samples_s": [round(t, 5) for t in per],
+                   "iters": iters[-1], "site_iterations_per_s": V * sum(iters) / (ms / 1e3),
+                   "theta": r["theta"], "F": r["F"], "plaquette": plaq, "ms_total": ms, "iters_all": iters,
+                   "ktimes": ktimes}
+            if prec == "fp64":
+                ctx.load(U_in, prec)
+                rh = ctx.iterate(1 << 30, 0.08, 1e-15, history_len=4096, **kw)
+                res["history"] = rh["history"][: rh["iters"] + 1]
+            res["error_vs_oracle"] = error_vs_oracle(res, golden)
+            results[name] = res
     clocks = clk.summary()
+
+    head = results[args.precision]
+    t_max, site_iters = reduce_over_ranks(head["ms_total"], V * sum(head["iters_all"]), ws, "cuda")
+    value = site_iters / (t_max / 1e3)
+
+    # roofline of every kernel of the headline schedule; the dominant kernel (largest share) is reported
+    hbm, sm_max, which = peaks()
     clk_hz = (clocks["sm_mhz"] or sm_max) * 1e6
     alu_peak = {"fp64": (FP64_FLOP_PER_CLK * clk_hz, "TFLOP/s", "152 SMs x 4 FP64 flop/clk"),
                 "fp32": (FP32_OPS_PER_CLK * clk_hz, "Tops/s (FP32-pipe operations)", "152 SMs x 128 FP32 ops/clk")}
-    kernels = {}
-    total_ms = sum(v[1] for v in ktimes.values())
-    for name, (n, kms) in ktimes.items():
-        b, f, kind = algorithmic(name, dims)
-        per = kms / n / 1e3
-        gbs = b / per / 1e9
-        d = {"launches": n, "ms_total": round(kms, 3), "share": round(kms / total_ms, 4),
-             "ms_per_launch": round(kms / n, 4), "GB_s": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4)}
-        if kind:
-            d["alu_kind"] = kind
-            d["alu_frac"] = round(f / per / alu_peak[kind][0], 4)
-        kernels[name] = d
+    kernels = kernel_table(head["ktimes"], dims, hbm, alu_peak)
     dom = max(kernels, key=lambda k: kernels[k]["ms_total"])
     dk = kernels[dom]
     b, f, kind = algorithmic(dom, dims)
     per = dk["ms_per_launch"] / 1e3
+    traffic = TRAFFIC_64.get(dom) if tuple(dims) == (64, 64, 64, 64) else None
     if kind and dk["alu_frac"] > dk["hbm_frac"]:
         pk, unit, src = alu_peak[kind]
         roof = {"bound": "alu", "achieved": round(f / per / 1e12, 4), "peak": round(pk / 1e12, 4),
-                "unit": unit, "frac": round(f / per / pk, 4),
-                "traffic": TRAFFIC_64.get(dom) if tuple(dims) == (64, 64, 64, 64) else None,
+                "unit": unit, "frac": round(f / per / pk, 4), "traffic": traffic,
                 "kernel": dom, "peak_source": "derived: %s x median SM clock under load" % src}
     else:
         roof = {"bound": "hbm", "achieved": round(b / per / 1e9, 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(b / per / 1e9 / hbm, 4),
-                "traffic": TRAFFIC_64.get(dom) if tuple(dims) == (64, 64, 64, 64) else None, "kernel": dom,
+                "frac": round(b / per / 1e9 / hbm, 4), "traffic": traffic, "kernel": dom,
                 "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % which}
 
-    # end to end through the C ABI from pinned host buffers (H2D + fix + D2H inside the timed region)
+    # end to end through the C ABI from pinned host buffers (H2D + fix + D2H inside the timed region):
+    # one untimed call, then three timed calls; the median is reported
     e2e = None
     if not args.no_e2e:
         work = torch.empty_like(host).pin_memory()
-        times = []
-        for rep in range(2):
+        samples = []
+        for rep in range(4):
             work.copy_(host)
             barrier()
             t0 = time.perf_counter()
             r = lat.fix(work.numpy(), 0.08, 1e-15, args.precision, theta_switch=args.theta_switch)
             dt = time.perf_counter() - t0
             if rep > 0:
-                times.append((dt, r["iters"]))
-        dt, it = times[0]
-        dt_max, work = reduce_over_ranks(dt, V * it, ws, "cuda")
+                samples.append((dt, r["iters"]))
+        dt, it = sorted(samples)[len(samples) // 2]
+        dt_max, work_all = reduce_over_ranks(dt, V * it, ws, "cuda")
         nbytes = 4 * V * 144 * ws  # every rank copies its own links in and out
-        e2e = {"value": work / dt_max, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
-               "time_to_theta_s": dt_max, "step": "one lgf_fix call on pinned host links"}
+        e2e = {"value": work_all / dt_max, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+               "time_to_theta_s": dt_max, "samples_s": [round(d, 4) for d, _ in samples],
+               "step": "one lgf_fix call on pinned host links (median of 3 timed calls after 1 untimed)"}
 
     if rank == 0:
-        gpu_launches = sum(v[0] for v in ktimes.values())
+        gpu_launches = sum(v[0] for v in head["ktimes"].values())
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": {"mixed": "f32+f64", "fp64": "f64", "fp32": "f32"}[args.precision],
                 "data": "synthetic", "config": config_of(args, dims, args.precision),
-                "iters_per_step": iters[0], "time_to_theta_s": {args.precision: t_max / args.steps / 1e3},
-                "theta": r["theta"], "F": r["F"],
-                "roofline": roof, "gpu_launches": gpu_launches, "clocks": clocks, "e2e": e2e,
-                "kernels": kernels}
-        if fp64:
-            line["time_to_theta_s"]["fp64"] = fp64["time_to_theta_s"]
-            line["fp64"] = fp64
-        if fast:
-            line["time_to_theta_s"]["mixed_fft32_final"] = fast["time_to_theta_s"]
-            line["mixed_fft32_final"] = fast
-        if spec:
-            line["time_to_theta_s"]["mixed_as_specified"] = spec["time_to_theta_s"]
-            line["mixed_as_specified"] = spec
+                "iters_per_step": head["iters"], "time_to_theta_s": {}, "theta": head["theta"], "F": head["F"],
+                "roofline": roof, "gpu_launches": gpu_launches, "clocks": clocks, "e2e": e2e, "kernels": kernels}
+        notes = {"mixed_as_specified": "theta_switch 1e-8, float-stage reprojection in double, double iterations "
+                                       "after the handover",
+                 "mixed_fft32_final": "double stage with the Fourier filter in float; links, Delta, g, update and "
+                                      "sums in double"}
+        for name, res in results.items():
+            line["time_to_theta_s"][name] = res["time_to_theta_s"]
+            out = {k: res[k] for k in ("time_to_theta_s", "time_to_theta_samples_s", "iters", "site_iterations_per_s",
+                                       "theta", "F", "plaquette", "error_vs_oracle")}
+            if name != args.precision:
+                out["kernels_ms"] = {k: round(v[1], 3) for k, v in
+                                     sorted(res["ktimes"].items(), key=lambda kv: -kv[1][1])}
+            if name in notes:
+                out["note"] = notes[name]
+            line[name] = out
+        line["error_vs_oracle"] = head["error_vs_oracle"]
         if not args.no_cpu:
-            line["cpu_baseline"] = cpu_baseline(dims, args, V)
+            line["cpu_baseline"] = cpu_baseline(dims, args, V, golden, head["iters"])
         print(json.dumps(line), flush=True)
     lat.close()
+    if lat_s is not None:
+        lat_s.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
 
