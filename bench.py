@@ -413,6 +413,29 @@ def run_batch(args):
                          "site_iterations_per_s": siters / dt,
                          "converged": sum(r["status"] == 0 for r in res), "iters_min": min(its),
                          "iters_max": max(its), "describe": b.describe()}
+    # the same 48 configurations fixed one after another, each by a single-configuration context (one
+    # context per shape, reused): what grouping and graph replay save, or cost, against separate fixes
+    for prec in ("mixed", "fp64"):
+        lats = {d: lgf.Lattice(d) for d in sorted(set(shapes))}
+        for d, lat in lats.items():
+            lat.set_stream(torch.cuda.current_stream())
+        for w, u in zip(work, inputs):
+            w.copy_(u)
+        for lat, w in ((lats[d], w) for d, w in zip(shapes, work)):  # warm-up: one fix per context
+            lat.fix(w, 0.08, 1e-15, prec)
+        for w, u in zip(work, inputs):
+            w.copy_(u)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        siters = 0
+        for d, w in zip(shapes, work):
+            r = lats[d].fix(w, 0.08, 1e-15, prec)
+            siters += int(np.prod(d)) * r["iters"]
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        for lat in lats.values():
+            lat.close()
+        out[prec]["sequential_single_contexts"] = {"time_to_theta_s": dt, "site_iterations_per_s": siters / dt}
     out["value"] = out["mixed"]["site_iterations_per_s"]
     return out
 

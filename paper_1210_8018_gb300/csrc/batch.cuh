@@ -239,7 +239,8 @@ lgf_status enter_residual_one(lgf_ctx *g, int j, double eps, bool narrow) {
   lgf_ctx *ctx = g;
   const int64_t V = g->V;
   if (narrow) {
-    k_narrow_link_planes<<<grid1(4 * V, NT), NT, 0, g->stream>>>(cfg_links(g->s64.U, g, j), cfg_links(g->s32.U, g, j), V);
+    k_narrow_link_planes<<<grid1(4 * V, NT), NT, 0, g->stream>>>(cfg_links(g->s64.U, g, j), cfg_links(g->s32.U, g, j), V,
+                                                                  0, 4 * V);
     CKL();
   }
   CK(cudaMemsetAsync(g->Rres + (int64_t)j * 72 * V, 0, sizeof(float) * 72 * (size_t)V, g->stream));

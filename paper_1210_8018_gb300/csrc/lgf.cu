@@ -104,6 +104,8 @@ struct lgf_ctx {
   Lattice L;
   int device = 0;
   cudaStream_t own_stream = nullptr, stream = nullptr;
+  cudaStream_t copy_stream = nullptr;  // host <-> device copies of links, pipelined with their conversion
+  cudaEvent_t cev[9] = {nullptr};      // chunk events of that pipeline (kPipelineChunks + 1)
   std::string err;
   bool poisoned = false;
   int smem_optin = 0;
@@ -755,7 +757,7 @@ lgf_status residual_begin(lgf_ctx *ctx) {
   TRY(alloc(ctx, &ctx->Kres, (size_t)9 * V * 2));
   if (!ctx->resid_base_ready) {
     TRY(timed_begin(ctx, kid<float>(KID_RESIDUAL_BASE)));
-    k_narrow_link_planes<<<grid1((int64_t)4 * V, NT), NT, 0, ctx->stream>>>(ctx->s64.U, ctx->s32.U, V);
+    k_narrow_link_planes<<<grid1((int64_t)4 * V, NT), NT, 0, ctx->stream>>>(ctx->s64.U, ctx->s32.U, V, 0, 4 * V);
     CKL();
     TRY(timed_end(ctx));
   }
@@ -815,16 +817,113 @@ lgf_status residual_rebuild(lgf_ctx *ctx) {
 template <typename T> lgf_status to_planes(lgf_ctx *ctx, const double *src, T *dst, int nmat) {
   TRY(timed_begin(ctx, kid<T>(KID_TO_PLANES)));
   const int np = nmat == 4 ? LinkStore<T>::planes : 9;
-  k_aos_to_planes<T><<<grid1((int64_t)nmat * ctx->V, NT), NT, 0, ctx->stream>>>(src, dst, ctx->V, nmat, np);
+  k_aos_to_planes<T><<<grid1((int64_t)nmat * ctx->V, NT), NT, 0, ctx->stream>>>(src, dst, ctx->V, nmat, np, 0,
+                                                                                (int64_t)nmat * ctx->V);
   CKL();
   return timed_end(ctx);
 }
 template <typename T> lgf_status from_planes(lgf_ctx *ctx, const T *src, double *dst, int nmat) {
   TRY(timed_begin(ctx, kid<T>(KID_FROM_PLANES)));
   const int np = nmat == 4 ? LinkStore<T>::planes : 9;
-  k_planes_to_aos<T><<<grid1((int64_t)nmat * ctx->V, NT), NT, 0, ctx->stream>>>(src, dst, ctx->V, nmat, np);
+  k_planes_to_aos<T><<<grid1((int64_t)nmat * ctx->V, NT), NT, 0, ctx->stream>>>(src, dst, ctx->V, nmat, np, 0,
+                                                                                (int64_t)nmat * ctx->V);
   CKL();
   return timed_end(ctx);
+}
+
+// Links from the caller's layout into the working planes for `precision`, for the links i0 .. i0 + n - 1 of
+// the 4V (mu-major): FP64 -> double planes; MIXED -> the double planes U0 kept for the handover and the float
+// links narrowed from them; FP32 -> float planes.
+lgf_status convert_links_in(lgf_ctx *ctx, const double *src, int precision, int64_t i0, int64_t n) {
+  const int64_t V = ctx->V;
+  if (precision == LGF_FP64) {
+    TRY(timed_begin(ctx, kid<double>(KID_TO_PLANES)));
+    k_aos_to_planes<double><<<grid1(n, NT), NT, 0, ctx->stream>>>(src, ctx->s64.U, V, 4, 9, i0, n);
+    CKL();
+    return timed_end(ctx);
+  }
+  if (precision == LGF_MIXED) {
+    TRY(timed_begin(ctx, kid<double>(KID_TO_PLANES)));
+    k_aos_to_planes<double><<<grid1(n, NT), NT, 0, ctx->stream>>>(src, ctx->U0, V, 4, 9, i0, n);
+    CKL();
+    TRY(timed_end(ctx));
+    TRY(timed_begin(ctx, kid<float>(KID_TO_PLANES)));
+    k_narrow_link_planes<<<grid1(n, NT), NT, 0, ctx->stream>>>(ctx->U0, ctx->s32.U, V, i0, n);
+    CKL();
+    return timed_end(ctx);
+  }
+  TRY(timed_begin(ctx, kid<float>(KID_TO_PLANES)));
+  k_aos_to_planes<float><<<grid1(n, NT), NT, 0, ctx->stream>>>(src, ctx->s32.U, V, 4, LinkStore<float>::planes, i0, n);
+  CKL();
+  return timed_end(ctx);
+}
+
+// Working planes (double, or float with row 2 rebuilt) -> the caller's layout, links i0 .. i0 + n - 1.
+lgf_status convert_links_out(lgf_ctx *ctx, bool from_float, double *dst, int64_t i0, int64_t n) {
+  const int64_t V = ctx->V;
+  if (from_float) {
+    TRY(timed_begin(ctx, kid<float>(KID_FROM_PLANES)));
+    k_planes_to_aos<float><<<grid1(n, NT), NT, 0, ctx->stream>>>(ctx->s32.U, dst, V, 4, LinkStore<float>::planes, i0,
+                                                                  n);
+  } else {
+    TRY(timed_begin(ctx, kid<double>(KID_FROM_PLANES)));
+    k_planes_to_aos<double><<<grid1(n, NT), NT, 0, ctx->stream>>>(ctx->s64.U, dst, V, 4, 9, i0, n);
+  }
+  CKL();
+  return timed_end(ctx);
+}
+
+// Host links are moved in chunks: the copy engine works on a second stream, and each chunk is converted on
+// the working stream as soon as it has arrived (loading) or copied out as soon as it has been converted
+// (storing), so the conversions overlap the copies. Links below kPipelineMinBytes go in one chunk.
+constexpr int kPipelineChunks = 8;
+constexpr size_t kPipelineMinBytes = (size_t)64 << 20;
+
+lgf_status ensure_copy_stream(lgf_ctx *ctx) {
+  if (!ctx->copy_stream) CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+  for (int c = 0; c <= kPipelineChunks; ++c)
+    if (!ctx->cev[c]) CK(cudaEventCreateWithFlags(&ctx->cev[c], cudaEventDisableTiming));
+  return LGF_OK;
+}
+
+lgf_status load_host_links(lgf_ctx *ctx, const double *host, int precision) {
+  const int64_t nl = 4 * ctx->V;
+  const size_t bytes = (size_t)nl * 144;
+  TRY(ensure_staging(ctx, &ctx->staging, &ctx->staging_bytes, bytes));
+  TRY(ensure_copy_stream(ctx));
+  const int nc = bytes >= kPipelineMinBytes ? kPipelineChunks : 1;
+  // the copies overwrite the staging buffer only after the working stream's earlier work on it
+  CK(cudaEventRecord(ctx->cev[kPipelineChunks], ctx->stream));
+  CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->cev[kPipelineChunks], 0));
+  for (int c = 0; c < nc; ++c) {
+    const int64_t i0 = nl * c / nc, i1 = nl * (c + 1) / nc;
+    CK(cudaMemcpyAsync(ctx->staging + i0 * 18, host + i0 * 18, (size_t)(i1 - i0) * 144, cudaMemcpyHostToDevice,
+                       ctx->copy_stream));
+    CK(cudaEventRecord(ctx->cev[c], ctx->copy_stream));
+    CK(cudaStreamWaitEvent(ctx->stream, ctx->cev[c], 0));
+    TRY(convert_links_in(ctx, ctx->staging, precision, i0, i1 - i0));
+  }
+  return LGF_OK;
+}
+
+lgf_status store_host_links(lgf_ctx *ctx, bool from_float, double *host) {
+  const int64_t nl = 4 * ctx->V;
+  const size_t bytes = (size_t)nl * 144;
+  TRY(ensure_staging(ctx, &ctx->staging, &ctx->staging_bytes, bytes));
+  TRY(ensure_copy_stream(ctx));
+  const int nc = bytes >= kPipelineMinBytes ? kPipelineChunks : 1;
+  for (int c = 0; c < nc; ++c) {
+    const int64_t i0 = nl * c / nc, i1 = nl * (c + 1) / nc;
+    TRY(convert_links_out(ctx, from_float, ctx->staging, i0, i1 - i0));
+    CK(cudaEventRecord(ctx->cev[c], ctx->stream));
+    CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->cev[c], 0));
+    CK(cudaMemcpyAsync(host + i0 * 18, ctx->staging + i0 * 18, (size_t)(i1 - i0) * 144, cudaMemcpyDeviceToHost,
+                       ctx->copy_stream));
+  }
+  // later work on the working stream (which may reuse the staging buffer) follows the copies
+  CK(cudaEventRecord(ctx->cev[kPipelineChunks], ctx->copy_stream));
+  CK(cudaStreamWaitEvent(ctx->stream, ctx->cev[kPipelineChunks], 0));
+  return LGF_OK;
 }
 
 lgf_status upload_hist(lgf_ctx *ctx, const lgf_options *opt) {
@@ -993,6 +1092,12 @@ void lgf_destroy(lgf_ctx *ctx) {
     cudaEventDestroy(e.first);
     cudaEventDestroy(e.second);
   }
+  if (ctx->copy_stream) {
+    cudaStreamSynchronize(ctx->copy_stream);
+    cudaStreamDestroy(ctx->copy_stream);
+  }
+  for (auto e : ctx->cev)
+    if (e) cudaEventDestroy(e);
   if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
   delete ctx;
 }
@@ -1014,9 +1119,11 @@ lgf_status lgf_load(lgf_ctx *ctx, const double *links, int precision) {
     return fail(ctx, LGF_EINVAL, "unknown precision");
   TRY(ensure_common(ctx));
   const int64_t V = ctx->V;
-  const size_t bytes = (size_t)4 * V * 9 * 16;
-  const double *src = nullptr;
-  TRY(input_ptr(ctx, links, bytes, &ctx->staging, &ctx->staging_bytes, &src));
+  if (!links) return fail(ctx, LGF_EINVAL, "null buffer");
+  const PtrKind kind = ptr_kind(links, ctx->device);
+  if (kind == PTR_OTHER_DEVICE) return fail(ctx, LGF_EINVAL, "device buffer belongs to another GPU than the context's");
+  if (kind == PTR_DEVICE && (((uintptr_t)links) & 15))
+    return fail(ctx, LGF_EINVAL, "device buffers must be 16-byte aligned");
   memset(&ctx->ctrl_host, 0, sizeof(Ctrl));
   ctx->ctrl_host.active = 1;
   ctx->ctrl_host.limit = 0;
@@ -1025,24 +1132,19 @@ lgf_status lgf_load(lgf_ctx *ctx, const double *links, int precision) {
   TRY(write_ctrl(ctx));
   if (precision == LGF_FP64) {
     TRY(setup_precision<double>(ctx, ctx->s64));
-    TRY(to_planes<double>(ctx, src, ctx->s64.U, 4));
-    TRY(launch_delta<double>(ctx, ctx->s64, 0, 0));
-    ctx->stage = LGF_FP64;
   } else {
     TRY(setup_precision<float>(ctx, ctx->s32));
     TRY(alloc(ctx, &ctx->Gacc, (size_t)ctx->nb * 6 * V * 2));
-    if (precision == LGF_MIXED) {
-      // the caller's links are read once: into the double planes kept for the handover, and the float
-      // links from those
-      TRY(alloc(ctx, &ctx->U0, (size_t)ctx->nb * 4 * 9 * V * 2));
-      TRY(to_planes<double>(ctx, src, ctx->U0, 4));
-      TRY(timed_begin(ctx, kid<float>(KID_TO_PLANES)));
-      k_narrow_link_planes<<<grid1((int64_t)4 * V, NT), NT, 0, ctx->stream>>>(ctx->U0, ctx->s32.U, V);
-      CKL();
-      TRY(timed_end(ctx));
-    } else {
-      TRY(to_planes<float>(ctx, src, ctx->s32.U, 4));
-    }
+    // mixed: the caller's links are read once, into the double planes kept for the handover, and the
+    // float links are narrowed from those
+    if (precision == LGF_MIXED) TRY(alloc(ctx, &ctx->U0, (size_t)ctx->nb * 4 * 9 * V * 2));
+  }
+  if (kind == PTR_HOST) TRY(load_host_links(ctx, links, precision));
+  else TRY(convert_links_in(ctx, links, precision, 0, 4 * V));
+  if (precision == LGF_FP64) {
+    TRY(launch_delta<double>(ctx, ctx->s64, 0, 0));
+    ctx->stage = LGF_FP64;
+  } else {
     TRY(timed_begin(ctx, kid<float>(KID_SET_IDENTITY)));
     k_set_identity<<<grid1(V, NT), NT, 0, ctx->stream>>>(ctx->Gacc, V);
     CKL();
@@ -1169,20 +1271,19 @@ lgf_status lgf_store(lgf_ctx *ctx, double *links) {
   TRY(check_ctx(ctx));
   if (!ctx->loaded) return fail(ctx, LGF_EINVAL, "lgf_store before lgf_load");
   const int64_t V = ctx->V;
-  const size_t bytes = (size_t)4 * V * 9 * 16;
-  double *dst = nullptr;
-  bool host = false;
-  TRY(output_ptr(ctx, links, bytes, &ctx->staging, &ctx->staging_bytes, &dst, &host));
+  if (!links) return fail(ctx, LGF_EINVAL, "null buffer");
+  const PtrKind kind = ptr_kind(links, ctx->device);
+  if (kind == PTR_OTHER_DEVICE) return fail(ctx, LGF_EINVAL, "device buffer belongs to another GPU than the context's");
+  if (kind == PTR_DEVICE && (((uintptr_t)links) & 15))
+    return fail(ctx, LGF_EINVAL, "device buffers must be 16-byte aligned");
   if (ctx->stage == kHostStageResidual) TRY(residual_rebuild(ctx));
-  if (ctx->stage == LGF_FP64) {
-    TRY(from_planes<double>(ctx, ctx->s64.U, dst, 4));
-  } else if (ctx->load_prec == LGF_MIXED) {
-    TRY(handover(ctx));
-    TRY(from_planes<double>(ctx, ctx->s64.U, dst, 4));
-  } else {
-    TRY(from_planes<float>(ctx, ctx->s32.U, dst, 4));
+  bool from_float = false;
+  if (ctx->stage != LGF_FP64) {
+    if (ctx->load_prec == LGF_MIXED) TRY(handover(ctx));
+    else from_float = true;
   }
-  if (host) CK(cudaMemcpyAsync(links, dst, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  if (kind == PTR_HOST) TRY(store_host_links(ctx, from_float, links));
+  else TRY(convert_links_out(ctx, from_float, links, 0, 4 * V));
   CK(cudaStreamSynchronize(ctx->stream));
   return LGF_OK;
 }
@@ -1211,7 +1312,7 @@ lgf_status lgf_measure(lgf_ctx *ctx, const double *links, double *theta, double 
   const int64_t V = ctx->V;
   const double *src = nullptr;
   TRY(input_ptr(ctx, links, (size_t)4 * V * 9 * 16, &ctx->staging, &ctx->staging_bytes, &src));
-  k_aos_to_planes<double><<<grid1(4 * V, NT), NT, 0, ctx->stream>>>(src, ctx->s64.U, V, 4, 9);
+  k_aos_to_planes<double><<<grid1(4 * V, NT), NT, 0, ctx->stream>>>(src, ctx->s64.U, V, 4, 9, 0, 4 * V);
   CKL();
   memset(&ctx->ctrl_host, 0, sizeof(Ctrl));
   TRY(write_ctrl(ctx));
@@ -1252,7 +1353,7 @@ template <typename T> static lgf_status unpack_field(lgf_ctx *ctx, State<T> &S, 
 template <typename T> static lgf_status step_delta(lgf_ctx *ctx, State<T> &S, const double *src, double *dst,
                                                    double *theta, double *F) {
   const int64_t V = ctx->V;
-  k_aos_to_planes<T><<<grid1(4 * V, NT), NT, 0, ctx->stream>>>(src, S.U, V, 4, LinkStore<T>::planes);
+  k_aos_to_planes<T><<<grid1(4 * V, NT), NT, 0, ctx->stream>>>(src, S.U, V, 4, LinkStore<T>::planes, 0, 4 * V);
   CKL();
   memset(&ctx->ctrl_host, 0, sizeof(Ctrl));
   TRY(write_ctrl(ctx));
@@ -1379,7 +1480,7 @@ template <typename T> static lgf_status step_gauge(lgf_ctx *ctx, State<T> &S, co
     TRY(pack_field<T>(ctx, S, src));
     TRY(launch_gauge<T>(ctx, S, alpha, 0));
   }
-  k_planes_to_aos<T><<<grid1(V, NT), NT, 0, ctx->stream>>>(S.G, dst, V, 1, 9);
+  k_planes_to_aos<T><<<grid1(V, NT), NT, 0, ctx->stream>>>(S.G, dst, V, 1, 9, 0, V);
   CKL();
   return LGF_OK;
 }
@@ -1409,16 +1510,16 @@ extern "C" lgf_status lgf_gauge(lgf_ctx *ctx, const double *dtilde, double alpha
 template <typename T> static lgf_status step_update(lgf_ctx *ctx, State<T> &S, const double *lsrc, const double *gsrc,
                                                     double *dst) {
   const int64_t V = ctx->V;
-  k_aos_to_planes<T><<<grid1(4 * V, NT), NT, 0, ctx->stream>>>(lsrc, S.U, V, 4, LinkStore<T>::planes);
+  k_aos_to_planes<T><<<grid1(4 * V, NT), NT, 0, ctx->stream>>>(lsrc, S.U, V, 4, LinkStore<T>::planes, 0, 4 * V);
   CKL();
-  k_aos_to_planes<T><<<grid1(V, NT), NT, 0, ctx->stream>>>(gsrc, S.G, V, 1, 9);
+  k_aos_to_planes<T><<<grid1(V, NT), NT, 0, ctx->stream>>>(gsrc, S.G, V, 1, 9, 0, V);
   CKL();
   if constexpr (std::is_same<T, double>::value) {
     k_a_from_g<NT><<<grid1(V, NT), NT, 0, ctx->stream>>>(S.G, S.A, V);
     CKL();
   }
   TRY(launch_update<T>(ctx, S, 0));
-  k_planes_to_aos<T><<<grid1(4 * V, NT), NT, 0, ctx->stream>>>(S.U, dst, V, 4, LinkStore<T>::planes);
+  k_planes_to_aos<T><<<grid1(4 * V, NT), NT, 0, ctx->stream>>>(S.U, dst, V, 4, LinkStore<T>::planes, 0, 4 * V);
   CKL();
   return LGF_OK;
 }

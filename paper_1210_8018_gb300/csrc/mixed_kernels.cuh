@@ -81,9 +81,10 @@ __global__ void __launch_bounds__(NT) k_update_fused_f32(float *__restrict__ U, 
 
 // Float links (rows 0 and 1, 6 planes per direction) from the double link planes (9 per direction),
 // rounded to nearest.
-__global__ void k_narrow_link_planes(const double *__restrict__ U64, float *__restrict__ U32, int64_t V) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= 4 * V) return;
+__global__ void k_narrow_link_planes(const double *__restrict__ U64, float *__restrict__ U32, int64_t V, int64_t idx0,
+                                     int64_t n) {
+  const int64_t idx = idx0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= idx0 + n || idx >= 4 * V) return;
   const int64_t mu = idx / V, s = idx - mu * V;
 #pragma unroll
   for (int e = 0; e < 6; ++e) {

@@ -712,11 +712,13 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 4 : 2)
 // Layout conversions between the caller's array-of-structures links / site fields (double) and the
 // working planes (T). These run once per load/store, not in the loop.
 // ---------------------------------------------------------------------------------------------
-// A: nmat*V matrices of 9 complex; Pl: planes [(m*np + e)*V + s], np = 9, or 6 (rows 0-1 of links)
+// A: nmat*V matrices of 9 complex; Pl: planes [(m*np + e)*V + s], np = 9, or 6 (rows 0-1 of links). The
+// launch converts the matrices idx0 .. idx0 + n - 1 (a chunk, when the copy from the host is pipelined).
 template <typename T>
-__global__ void k_aos_to_planes(const double *__restrict__ A, T *__restrict__ Pl, int64_t V, int nmat, int np) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)nmat * V) return;
+__global__ void k_aos_to_planes(const double *__restrict__ A, T *__restrict__ Pl, int64_t V, int nmat, int np,
+                                int64_t idx0, int64_t n) {
+  const int64_t idx = idx0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= idx0 + n || idx >= (int64_t)nmat * V) return;
   const int64_t m = idx / V, s = idx - m * V;
   const double2 *src = reinterpret_cast<const double2 *>(A) + idx * 9;
   for (int e = 0; e < np; ++e) {
@@ -726,9 +728,10 @@ __global__ void k_aos_to_planes(const double *__restrict__ A, T *__restrict__ Pl
 }
 
 template <typename T>
-__global__ void k_planes_to_aos(const T *__restrict__ Pl, double *__restrict__ A, int64_t V, int nmat, int np) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)nmat * V) return;
+__global__ void k_planes_to_aos(const T *__restrict__ Pl, double *__restrict__ A, int64_t V, int nmat, int np,
+                                int64_t idx0, int64_t n) {
+  const int64_t idx = idx0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= idx0 + n || idx >= (int64_t)nmat * V) return;
   const int64_t m = idx / V, s = idx - m * V;
   double2 *dst = reinterpret_cast<double2 *>(A) + idx * 9;
   m3<T> u;
