@@ -168,14 +168,26 @@ struct lgf_batch {
   bool poisoned = false;
   bool autotune = true;
   std::string tuned[2];  // description of the tuned FFT plans per group, double / float
+  cudaStream_t body_stream = nullptr;  // captures the bodies of the graph's conditional nodes
   cudaGraphExec_t graph = nullptr;
   int graph_prec = -1, graph_chunk = 0;
   double graph_alpha = 0;
-  int launches_per_replay = 0;
+  int launches_per_replay = 0;  // kernels in the graph (those inside the IF bodies run only when guarded in)
+  int guarded_stages = 0;       // IF nodes: one per (iteration, group, stage)
   long graph_replays = 0;
 };
 
 namespace {
+
+// Condition of the IF node that guards one stage's iteration of a group in the replayed graph: 1 when some
+// configuration of the group is active in that stage (0 float, 1 double, kStageResidual), else 0, and then
+// none of that iteration's kernels is launched. The kernels inside still check each configuration.
+__global__ void k_stage_condition(cudaGraphConditionalHandle h, const Ctrl *ctrl, int nb, int stage) {
+  int any = 0;
+  for (int j = threadIdx.x; j < nb; j += 32) any |= (ctrl[j].active && ctrl[j].stage == stage) ? 1 : 0;
+  any = __any_sync(0xffffffffu, any);
+  if (threadIdx.x == 0) cudaGraphSetConditional(h, any ? 1u : 0u);
+}
 
 lgf_status bfail(lgf_batch *b, lgf_status st, const std::string &msg) {
   if (b) {
@@ -183,6 +195,43 @@ lgf_status bfail(lgf_batch *b, lgf_status st, const std::string &msg) {
     if (st == LGF_ECUDA) b->poisoned = true;
   }
   return st;
+}
+
+// Appends to the graph being captured on b->stream one stage's iteration of group g, guarded by an IF node:
+// a one-warp kernel sets the condition from the group's loop controls, and the iteration's kernels form the
+// body (captured on b->body_stream), so a stage that no configuration of the group is in costs that one small
+// launch instead of a full launch of every kernel of the iteration.
+template <typename Fn> lgf_status add_guarded_stage(lgf_batch *b, lgf_ctx *g, int stage, Fn &&body) {
+  lgf_ctx *ctx = g;
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t cg = nullptr;
+  const cudaGraphNode_t *deps = nullptr;
+  size_t nd = 0;
+  CK(cudaStreamGetCaptureInfo(b->stream, &cs, nullptr, &cg, nullptr, nullptr, nullptr));
+  cudaGraphConditionalHandle h;
+  CK(cudaGraphConditionalHandleCreate(&h, cg, 0, cudaGraphCondAssignDefault));
+  k_stage_condition<<<1, 32, 0, b->stream>>>(h, g->ctrl, g->nb, stage);
+  CKL();
+  CK(cudaStreamGetCaptureInfo(b->stream, &cs, nullptr, &cg, &deps, nullptr, &nd));
+  cudaGraphNodeParams p = {};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = h;
+  p.conditional.type = cudaGraphCondTypeIf;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  CK(cudaGraphAddNode(&node, cg, deps, nullptr, nd, &p));
+  CK(cudaStreamUpdateCaptureDependencies(b->stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  cudaGraph_t bodyg = p.conditional.phGraph_out[0];
+  CK(cudaStreamBeginCaptureToGraph(b->body_stream, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  cudaStream_t saved = g->stream;
+  g->stream = b->body_stream;
+  const lgf_status st = body();
+  g->stream = saved;
+  cudaGraph_t out = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(b->body_stream, &out);
+  if (st != LGF_OK) return st;
+  if (e != cudaSuccess) return fail(ctx, LGF_ECUDA, std::string("body capture: ") + cudaGetErrorString(e));
+  return LGF_OK;
 }
 
 #define BCK(call)                                                                                 \
@@ -227,7 +276,8 @@ lgf_status handover_one(lgf_ctx *g, int j, bool base) {
   CKL();
   k_transform_from_q<NT><<<grid1(g->V, NT), NT, 0, g->stream>>>(cfg_links(g->U0, g, j), cfg_links(g->s64.U, g, j),
                                                                 cfg_mat(g->s64.G, g, j), g->L,
-                                                                base ? cfg_links(g->s32.U, g, j) : nullptr);
+                                                                base ? cfg_links(g->s32.U, g, j) : nullptr,
+                                                                g->handover_split[0], g->handover_split[1]);
   CKL();
   return LGF_OK;
 }
@@ -267,7 +317,7 @@ lgf_status rebuild_one(lgf_ctx *g, int j) {
   CKL();
   k_update<double, NT_UPDATE64><<<dim3(grid1(V, NT_UPDATE64), 1, 1), NT_UPDATE64, update_smem_bytes<NT_UPDATE64>(),
                                   g->stream>>>(cfg_links(g->s64.U, g, j), cfg_mat(g->s64.G, g, j), A, g->L, g->ctrl + j,
-                                               0, 0, g->small_step ? 1 : 0);
+                                               0, 0, g->small_step ? 1 : 0, g->update_split[0], g->update_split[1]);
   CKL();
   return LGF_OK;
 }
@@ -296,7 +346,9 @@ lgf_status lgf_batch_create(int n, const int *dims, lgf_batch **out) {
     b->group_of.push_back(g);
     b->index_of.push_back(counts[g]++);
   }
-  if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+  if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->body_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    if (b->stream) cudaStreamDestroy(b->stream);
     delete b;
     return fail(nullptr, LGF_ECUDA, "cudaStreamCreate failed");
   }
@@ -325,6 +377,7 @@ void lgf_batch_destroy(lgf_batch *b) {
     lgf_destroy(c);
   }
   if (b->stream) cudaStreamDestroy(b->stream);
+  if (b->body_stream) cudaStreamDestroy(b->body_stream);
   delete b;
 }
 
@@ -405,37 +458,33 @@ lgf_status lgf_batch_fix(lgf_batch *b, double *const *links, double alpha, doubl
     b->graph = nullptr;
     for (lgf_ctx *g : b->groups) g->timing = false;
     BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    b->guarded_stages = 0;
     int launches = 0;
-    for (int k = 0; k < chunk; ++k)
+    lgf_status cst = LGF_OK;
+    std::string cmsg;
+    for (int k = 0; k < chunk && cst == LGF_OK; ++k)
       for (lgf_ctx *g : b->groups) {
-        if (has_float) {
-          const lgf_status st = launch_iteration_float(g, alpha, k == chunk - 1);
-          launches += (int)g->s32.passes.size() + 2;
-          if (st != LGF_OK) {
-            cudaGraph_t junk;
-            cudaStreamEndCapture(b->stream, &junk);
-            return bfail(b, st, g->err);
-          }
+        if (has_float && cst == LGF_OK) {
+          cst = add_guarded_stage(b, g, 0, [&]() { return launch_iteration_float(g, alpha, k == chunk - 1); });
+          launches += (int)g->s32.passes.size() + 3;
         }
-        if (has_double) {
-          const lgf_status st = launch_iteration<double>(g, g->s64, alpha);
-          launches += (int)g->s64.passes.size() + 3;
-          if (st != LGF_OK) {
-            cudaGraph_t junk;
-            cudaStreamEndCapture(b->stream, &junk);
-            return bfail(b, st, g->err);
-          }
+        if (has_double && cst == LGF_OK) {
+          cst = add_guarded_stage(b, g, 1, [&]() { return launch_iteration<double>(g, g->s64, alpha); });
+          launches += (int)g->s64.passes.size() + 4;
         }
-        if (prec == LGF_MIXED && g->residual) {
-          const lgf_status st = launch_iteration_residual(g, alpha);
-          launches += (int)g->s32.passes.size() + 2;
-          if (st != LGF_OK) {
-            cudaGraph_t junk;
-            cudaStreamEndCapture(b->stream, &junk);
-            return bfail(b, st, g->err);
-          }
+        if (prec == LGF_MIXED && g->residual && cst == LGF_OK) {
+          cst = add_guarded_stage(b, g, kStageResidual, [&]() { return launch_iteration_residual(g, alpha); });
+          launches += (int)g->s32.passes.size() + 3;
         }
+        if (cst != LGF_OK && cmsg.empty()) cmsg = g->err;
+        b->guarded_stages += (has_float ? 1 : 0) + (has_double ? 1 : 0) + (prec == LGF_MIXED && g->residual ? 1 : 0);
       }
+    if (cst != LGF_OK) {
+      cudaGraph_t junk = nullptr;
+      cudaStreamEndCapture(b->stream, &junk);
+      if (junk) cudaGraphDestroy(junk);
+      return bfail(b, cst, cmsg.empty() ? "graph capture failed" : cmsg);
+    }
     cudaGraph_t graph;
     BCK(cudaStreamEndCapture(b->stream, &graph));
     BCK(cudaGraphInstantiate(&b->graph, graph, 0));
@@ -558,6 +607,7 @@ lgf_status lgf_batch_describe(const lgf_batch *b, char *buf, int len) {
   }
   s += "], \"fft_f64\": \"" + b->tuned[0] + "\", \"fft_f32\": \"" + b->tuned[1] +
        "\", \"launches_per_replay\": " + std::to_string(b->launches_per_replay) +
+       ", \"guarded_stages\": " + std::to_string(b->guarded_stages) +
        ", \"graph_replays\": " + std::to_string(b->graph_replays) + "}";
   std::snprintf(buf, (size_t)len, "%s", s.c_str());
   return LGF_OK;

@@ -144,6 +144,8 @@ struct lgf_ctx {
   bool residual = true;      // mixed: residual stage after the handover (LGF_RESIDUAL=0: double iterations)
   bool resid_off = false;    // this load: a rebuild made no progress, the double stage continues
   bool handover_fp64 = false;  // mixed handover transform in FP64 instead of 61-bit fixed point
+  int handover_split[2] = {2, 2};  // links per site in FP64 (even, odd warps), the rest in fixed point
+  int update_split[2] = {2, 2};    // the same for the general (large-step) form of the double update
   bool reunit_fp64 = false;    // float stages: periodic projection onto SU(3) in double instead of float
   bool resid_base_ready = false;  // the float link planes hold the double links rounded (by the handover)
   double resid_theta0 = 0;  // theta of the residual stage's base links
@@ -637,10 +639,11 @@ template <typename T> lgf_status launch_update(lgf_ctx *ctx, State<T> &S, int ch
   if constexpr (std::is_same<T, double>::value) {
     k_update<double, NT_UPDATE64><<<dim3(grid1(ctx->V, NT_UPDATE64), 1, ctx->nb), NT_UPDATE64,
                                     update_smem_bytes<NT_UPDATE64>(), ctx->stream>>>(
-        S.U, S.G, S.A, ctx->L, ctx->ctrl, check_active, kid<T>(KID_UPDATE), ctx->small_step ? 1 : 0);
+        S.U, S.G, S.A, ctx->L, ctx->ctrl, check_active, kid<T>(KID_UPDATE), ctx->small_step ? 1 : 0,
+        ctx->update_split[0], ctx->update_split[1]);
   } else {
     k_update<T, NT><<<dim3(grid1(ctx->V, NT), 1, ctx->nb), NT, 0, ctx->stream>>>(S.U, S.G, nullptr, ctx->L, ctx->ctrl,
-                                                                               check_active, kid<T>(KID_UPDATE), 0);
+                                                                               check_active, kid<T>(KID_UPDATE), 0, 0, 0);
   }
   CKL();
   return timed_end(ctx);
@@ -725,7 +728,8 @@ lgf_status handover(lgf_ctx *ctx, bool write_base = false) {
                                                                    write_base ? ctx->s32.U : nullptr);
   else
     k_transform_from_q<NT><<<grid1(ctx->V, NT), NT, 0, ctx->stream>>>(ctx->U0, ctx->s64.U, ctx->s64.G, ctx->L,
-                                                                     write_base ? ctx->s32.U : nullptr);
+                                                                     write_base ? ctx->s32.U : nullptr,
+                                                                     ctx->handover_split[0], ctx->handover_split[1]);
   CKL();
   ctx->resid_base_ready = write_base;
   return timed_end(ctx);
@@ -799,7 +803,7 @@ lgf_status residual_rebuild(lgf_ctx *ctx) {
   TRY(timed_begin(ctx, kid<double>(KID_RESIDUAL_REBUILD)));
   k_update<double, NT_UPDATE64><<<dim3(grid1(ctx->V, NT_UPDATE64), 1, 1), NT_UPDATE64, update_smem_bytes<NT_UPDATE64>(),
                                   ctx->stream>>>(S.U, S.G, S.A, ctx->L, ctx->ctrl, 0, kid<double>(KID_RESIDUAL_REBUILD),
-                                                 ctx->small_step ? 1 : 0);
+                                                 ctx->small_step ? 1 : 0, ctx->update_split[0], ctx->update_split[1]);
   CKL();
   TRY(timed_end(ctx));
   Ctrl &c = ctx->ctrl_host;
@@ -1025,6 +1029,20 @@ static lgf_status create_ctx(const int n[4], int nb, lgf_ctx **out) {
     ctx->residual = !(rs && rs[0] == '0');
     const char *hf = std::getenv("LGF_HANDOVER_FP64");
     ctx->handover_fp64 = hf && hf[0] == '1';
+    // LGF_HANDOVER_SPLIT=ab (two digits 0-4): links per site that the handover transform forms in FP64 in
+    // even and in odd warps, the others in 61-bit fixed point (default 22; 00 is fixed point alone)
+    const char *hs = std::getenv("LGF_HANDOVER_SPLIT");
+    if (hs && hs[0] >= '0' && hs[0] <= '4' && hs[1] >= '0' && hs[1] <= '4') {
+      ctx->handover_split[0] = hs[0] - '0';
+      ctx->handover_split[1] = hs[1] - '0';
+    }
+    // LGF_UPDATE_SPLIT=ab: the same for the general (large-step) form of the double update (default 22;
+    // 44 is FP64 alone, 00 fixed point alone)
+    const char *us = std::getenv("LGF_UPDATE_SPLIT");
+    if (us && us[0] >= '0' && us[0] <= '4' && us[1] >= '0' && us[1] <= '4') {
+      ctx->update_split[0] = us[0] - '0';
+      ctx->update_split[1] = us[1] - '0';
+    }
     const char *rf = std::getenv("LGF_REUNIT_FP64");
     ctx->reunit_fp64 = rf && rf[0] == '1';
   }

@@ -148,74 +148,44 @@ __global__ void __launch_bounds__(NT) k_transform_from(const double *__restrict_
   }
 }
 
-// The same transform in 64-bit fixed point with 61 fractional bits (Q61), on the integer pipe, which on
-// this GPU runs many times faster than the FP64 pipe. Every entry of an SU(3) matrix, of a product of
-// two, and every partial sum formed here is at most 1 in magnitude (the partial sums are bounded by
-// sum_k |a_k| |b_k| <= |a| |b| = 1 for unit rows and columns), so Q61 values stay near or below 2^61
-// and the integer sums never overflow. A product splits each factor into a signed high limb and a
-// 31-bit low limb, so the three partial products it keeps are 32 x 32 -> 64-bit multiplies; the
-// dropped low product and the truncation leave an error below 2^-59, and the result, rounded once to
-// double, is exact to FP64 rounding.
-__device__ __forceinline__ long long to_q61(double x) {  // x 2^61 toward zero, |x| < 2
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const int ed = (int)((b >> 52) & 0x7FF);
-  const unsigned long long m = (b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
-  const int sh = ed - 1014;  // x 2^61 = m 2^(ed - 1075 + 61)
-  unsigned long long q = sh >= 0 ? m << (sh & 15) : (sh > -64 ? m >> (-sh) : 0ull);
-  if (ed == 0) q = 0ull;
-  return (long long)b < 0 ? -(long long)q : (long long)q;
-}
-__device__ __forceinline__ double from_q61(long long q) {  // q 2^-61, rounded to nearest (ties to even)
-  if (q == 0) return 0.0;
-  const unsigned long long sign = q < 0 ? 0x8000000000000000ull : 0ull;
-  unsigned long long m = q < 0 ? (unsigned long long)(-q) : (unsigned long long)q;
-  const int lz = __clzll((long long)m);
-  m <<= lz;  // leading one at bit 63, of weight 2^(2 - lz)
-  unsigned long long mant = m >> 11;
-  const unsigned long long rest = m & 0x7FFull;
-  if (rest > 0x400ull || (rest == 0x400ull && (mant & 1ull))) ++mant;
-  int e = 2 - lz;
-  if (mant >> 53) {
-    mant >>= 1;
-    ++e;
+// Q61 arithmetic (to_q61, mul_q61, cq_mac, from_q61, ...): q61.cuh.
+
+// The link mu of site s in FP64: Udst = G(x) Usrc G^+(x + mu), rows 0-1 by products, row 2 = conj(row0 x row1).
+__device__ __forceinline__ void transform_link_fp64(const double *__restrict__ Usrc, double *__restrict__ Udst,
+                                                    const double *__restrict__ G, int64_t V, int64_t s, int64_t sf,
+                                                    int64_t off, float *__restrict__ U32, int mu) {
+  m3<double> gx, u, gy, t;
+#pragma unroll
+  for (int e = 0; e < 9; ++e) {
+    gx.e[e] = e < 6 ? ldg(G, (int64_t)e * V + s) : cx<double>{0.0, 0.0};  // rows 0-1 are used
+    u.e[e] = ldg(Usrc, off + (int64_t)e * V + s);
+    gy.e[e] = ldg(G, (int64_t)e * V + sf);
   }
-  return __longlong_as_double((long long)(sign | ((unsigned long long)(e + 1023) << 52) |
-                                          (mant & 0x000FFFFFFFFFFFFFull)));
-}
-__device__ __forceinline__ long long mul_q61(long long a, long long b) {
-  const int ah = (int)(a >> 31), bh = (int)(b >> 31);                       // |.| <= 2^30
-  const int al = (int)(a & 0x7FFFFFFFll), bl = (int)(b & 0x7FFFFFFFll);     // [0, 2^31)
-  const long long cross = (long long)ah * bl + (long long)al * bh;         // |.| < 2^62
-  return (((long long)ah * bh) << 1) + (cross >> 30);
-}
-struct cq {
-  long long r, i;
-};
-__device__ __forceinline__ cq to_cq(cx<double> v) { return {to_q61(v.r), to_q61(v.i)}; }
-__device__ __forceinline__ void cq_mac(cq &acc, cq a, cq b) {  // acc += a b
-  acc.r += mul_q61(a.r, b.r) - mul_q61(a.i, b.i);
-  acc.i += mul_q61(a.r, b.i) + mul_q61(a.i, b.r);
-}
-__device__ __forceinline__ void cq_mac_cj(cq &acc, cq a, cq b) {  // acc += a conj(b)
-  acc.r += mul_q61(a.r, b.r) + mul_q61(a.i, b.i);
-  acc.i += mul_q61(a.i, b.r) - mul_q61(a.r, b.i);
-}
-__device__ __forceinline__ cq cq_cross_cj(cq a, cq b, cq c, cq d) {  // conj(a b - c d)
-  cq t = {0, 0};
-  cq_mac(t, a, b);
-  cq_mac(t, {-c.r, -c.i}, d);
-  return {t.r, -t.i};
+  mul_rows01(gx, u, t);
+  mul_adj_rows01(t, gy, u);
+  complete_row2(u);
+#pragma unroll
+  for (int e = 0; e < 9; ++e) st(Udst, off + (int64_t)e * V + s, u.e[e]);
+  if (U32) {
+#pragma unroll
+    for (int e = 0; e < 6; ++e) st(U32, (int64_t)(mu * 6 + e) * V + s, mkc(narrow_bits(u.e[e].r), narrow_bits(u.e[e].i)));
+  }
 }
 
+// The four links of a site split between the two forms: the first fp64_even (in even warps) or fp64_odd
+// (in odd warps) directions in FP64, the others in Q61. The FP64 pipe and the integer pipes then work at
+// the same time on different warps; both forms are exact to FP64 rounding. fp64_even = fp64_odd = 0 is
+// the fixed-point form alone.
 template <int NT>
 __global__ void __launch_bounds__(NT, 2) k_transform_from_q(const double *__restrict__ Usrc, double *__restrict__ Udst,
                                                         const double *__restrict__ G, Lattice L,
-                                                        float *__restrict__ U32) {
+                                                        float *__restrict__ U32, int fp64_even, int fp64_odd) {
   const int64_t V = L.V;
   const int64_t s = (int64_t)blockIdx.x * NT + threadIdx.x;
   if (s >= V) return;
   int c[4];
   site_coords(L, s, c);
+  const int nf = ((threadIdx.x >> 5) & 1) ? fp64_odd : fp64_even;  // uniform within a warp
   cq gx[6];  // rows 0-1 of G(x): the rows of the result that are formed (row 2 follows from them)
 #pragma unroll
   for (int e = 0; e < 6; ++e) gx[e] = to_cq(ldg(G, (int64_t)e * V + s));
@@ -223,6 +193,10 @@ __global__ void __launch_bounds__(NT, 2) k_transform_from_q(const double *__rest
   for (int mu = 0; mu < 4; ++mu) {
     const int64_t sf = site_fwd(L, s, mu, c[mu]);
     const int64_t off = (int64_t)mu * 9 * V;
+    if (mu < nf) {
+      transform_link_fp64(Usrc, Udst, G, V, s, sf, off, U32, mu);
+      continue;
+    }
     cq t[6], o[9];
     // rows 0-1 of G(x) U, one column of U at a time
 #pragma unroll

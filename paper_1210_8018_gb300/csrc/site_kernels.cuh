@@ -15,6 +15,7 @@
 #pragma once
 #include <type_traits>
 
+#include "q61.cuh"
 #include "su3.cuh"
 
 namespace lgf {
@@ -624,10 +625,60 @@ __device__ __forceinline__ void update_link_general(double *plane, const double 
   store_link(plane, V, s, o);
 }
 
+// The same general-step product in 61-bit fixed point (q61.cuh) on the integer pipe: rows 0 and 1 of
+// g(x) U g^+(x+mu) exact to FP64 rounding, row 2 = conj(row0 x row1) in fixed point.
+template <int NT>
+__device__ __forceinline__ void update_link_general_q(double *plane, const double *G, int64_t V, int64_t s,
+                                                      int64_t sf, const double2 *bu) {
+  cq t[6];
+  {
+    cq gx[6];
+#pragma unroll
+    for (int e = 0; e < 6; ++e) gx[e] = to_cq(ldg(G, (int64_t)e * V + s));
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const cq u0 = to_cq(from_vec<double>(bu[j * NT + threadIdx.x]));
+      const cq u1 = to_cq(from_vec<double>(bu[(3 + j) * NT + threadIdx.x]));
+      const cq u2 = to_cq(from_vec<double>(bu[(6 + j) * NT + threadIdx.x]));
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        cq a = {0, 0};
+        cq_mac(a, gx[3 * i], u0);
+        cq_mac(a, gx[3 * i + 1], u1);
+        cq_mac(a, gx[3 * i + 2], u2);
+        t[3 * i + j] = a;
+      }
+    }
+  }
+  cq o[9];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const cq g0 = to_cq(ldg(G, (int64_t)(3 * j) * V + sf));
+    const cq g1 = to_cq(ldg(G, (int64_t)(3 * j + 1) * V + sf));
+    const cq g2 = to_cq(ldg(G, (int64_t)(3 * j + 2) * V + sf));
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      cq a = {0, 0};
+      cq_mac_cj(a, t[3 * i], g0);
+      cq_mac_cj(a, t[3 * i + 1], g1);
+      cq_mac_cj(a, t[3 * i + 2], g2);
+      o[3 * i + j] = a;
+    }
+  }
+  o[6] = cq_cross_cj(o[1], o[5], o[2], o[4]);
+  o[7] = cq_cross_cj(o[2], o[3], o[0], o[5]);
+  o[8] = cq_cross_cj(o[0], o[4], o[1], o[3]);
+#pragma unroll
+  for (int e = 0; e < 9; ++e) st(plane, (int64_t)e * V + s, cx<double>{from_q61(o[e].r), from_q61(o[e].i)});
+}
+
+// Double links: general steps are split between the FP64 pipe (the first fp64_even or fp64_odd directions
+// of a site, in even or odd warps) and the integer pipe (the others, in Q61), so that both pipes work at the
+// same time; both forms are exact to FP64 rounding.
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 4 : 2)
     k_update(T *__restrict__ U, const T *__restrict__ G, const float *__restrict__ A, Lattice L, const Ctrl *ctrl,
-             int check_active, int tkid, int allow_small) {
+             int check_active, int tkid, int allow_small, int fp64_even, int fp64_odd) {
   const int64_t V = L.V;
   {
     const int cfg = blockIdx.z;
@@ -684,7 +735,9 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 4 : 2)
         update_link_small<NT>(plane, V, s, sa, bu0, u, b);
         if (mu < 3) fetch_u<NT>(plane + pstride, V, s, bu0);
       } else {
-        update_link_general<NT>(plane, G, V, s, sf, bu);
+        const int nf = ((threadIdx.x >> 5) & 1) ? fp64_odd : fp64_even;  // uniform within a warp
+        if (mu < nf) update_link_general<NT>(plane, G, V, s, sf, bu);
+        else update_link_general_q<NT>(plane, G, V, s, sf, bu);
         if (mu < 3) fetch_link<NT>(plane + pstride, A, V, s, site_fwd(L, s, mu + 1, c[mu + 1]), bu0, bb);
       }
     }

@@ -81,6 +81,22 @@ def test_small_step_form_at_fp64_rounding(lgf, dims, size, monkeypatch):
     assert float(np.abs(uu).max()) < 1e-14
 
 
+@pytest.mark.parametrize("split", ["00", "21", "44", "13"])
+def test_general_form_fixed_point_and_fp64_splits(lgf, split, monkeypatch):
+    """Large steps (Haar-random g): the general form splits a site's four directions between FP64 products and
+    61-bit fixed-point products (LGF_UPDATE_SPLIT: FP64 directions in even and odd warps). Every split agrees
+    with the oracle's gauge transformation at the FP64 rounding level of the product form."""
+    monkeypatch.setenv("LGF_UPDATE_SPLIT", split)
+    dims = (8, 8, 8, 8)
+    U = synth.config(dims, 45, 0.6)
+    g = np.ascontiguousarray(synth.config(dims, 46, 0.0)[0])  # random SU(3) matrices h(x) h^+(x + x-hat)
+    U_ref = oracle.gauge_transform(U, g)
+    out = run_update(lgf, dims, U, g, monkeypatch, False)  # no warp is small: every link takes the general form
+    assert float(np.abs(out - U_ref).max()) <= 1e-14
+    uu = np.einsum("...ij,...kj->...ik", out, out.conj()) - np.eye(3)
+    assert float(np.abs(uu).max()) < 1e-14
+
+
 @pytest.mark.parametrize("dims", [(8, 8, 8, 8), (3, 5, 4, 2)])
 def test_mixed_warps(lgf, dims, monkeypatch):
     """Small g everywhere except Haar-random g on the x = 0 sites of every other (y, z, t) row: warps

@@ -99,9 +99,12 @@ def test_mixed_float_stage_hands_over_when_theta_stalls(lgf):
     assert oracle.theta(oracle.delta(Uf)) < 1e-15
 
 
-def test_handover_fixed_point_matches_fp64(lgf, monkeypatch):
-    """The handover links G U0 G^+(x+mu) formed in 61-bit fixed point agree with the FP64 product to a few
-    units of the FP64 rounding, and both are gauge-equivalent to the input."""
+@pytest.mark.parametrize("split", ["00", "21", "44", "13"])
+def test_handover_fixed_point_matches_fp64(lgf, monkeypatch, split):
+    """The handover links G U0 G^+(x+mu) formed in 61-bit fixed point, or split between fixed point and FP64
+    per direction (LGF_HANDOVER_SPLIT: FP64 directions in even and odd warps), agree with the FP64 product to
+    a few units of the FP64 rounding, and all are gauge-equivalent to the input."""
+    monkeypatch.setenv("LGF_HANDOVER_SPLIT", split)
     dims = (8, 8, 4, 6)
     U = synth.config(dims, 9, 0.6)
 
