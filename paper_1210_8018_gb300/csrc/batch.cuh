@@ -260,9 +260,14 @@ template <typename T> lgf_status delta_one(lgf_ctx *g, State<T> &S, int j) {
   lgf_ctx *ctx = g;
   return with_fft_type<T>(g, [&](auto tag) -> lgf_status {
     using FT = decltype(tag);
-    k_delta<T, NT, FT><<<dim3(g->nblocks_site, 1, 1), NT, 0, g->stream>>>(
-        cfg_links(S.U, g, j), reinterpret_cast<FT *>(cfg_packed(S.P, g, j)),
-        g->partials + (int64_t)j * 2 * g->nblocks_site, g->ctrl + j, g->L, 0, 0, 0);
+    if constexpr (std::is_same<T, float>::value)
+      k_delta_f32<NT><<<dim3(g->nblocks_site, 1, 1), NT, 0, g->stream>>>(
+          cfg_links(S.U, g, j), cfg_packed(S.P, g, j), g->partials + (int64_t)j * 2 * g->nblocks_site, g->ctrl + j,
+          g->L, 0, 0, 0);
+    else
+      k_delta<T, NT, FT><<<dim3(g->nblocks_site, 1, 1), NT, 0, g->stream>>>(
+          cfg_links(S.U, g, j), reinterpret_cast<FT *>(cfg_packed(S.P, g, j)),
+          g->partials + (int64_t)j * 2 * g->nblocks_site, g->ctrl + j, g->L, 0, 0, 0);
     CKL();
     return LGF_OK;
   });

@@ -18,4 +18,12 @@ template <typename FT> const void *fft_generic_kernel();
 // resident blocks), except in IEEE double, where four fields share the weights of the FP64 pipe.
 template <typename FT> constexpr int filter_fields_per_block() { return std::is_same<FT, double>::value ? 4 : 1; }
 
+// Passes that prefetch the next tile into registers while the current one is transformed: the float z
+// passes (forward, inverse; measured at 64^4: 0.19 -> 0.17 ms per pass). The xy pass and the t pass with
+// the filter gained nothing from it in float (the t pass lost resident blocks to the extra registers),
+// and the double-float and double passes are bound by arithmetic: those take one tile per block.
+template <typename FT, int KIND, int MODE> __host__ __device__ constexpr bool prefetch_tiles() {
+  return std::is_same<FT, float>::value && KIND == 2 && MODE != 2;
+}
+
 }  // namespace lgf

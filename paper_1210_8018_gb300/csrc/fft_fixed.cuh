@@ -88,13 +88,15 @@ template <typename T, int N> __device__ __forceinline__ void load_twiddles(cx<T>
   for (int k = threadIdx.x; k < N; k += blockDim.x) dst[k] = s[k];
 }
 
+
 // ---------------------------------------------------------------------------------------------
-// xy plane pass: the 2D transform of one (z, t) plane of one packed field. Tile [NY][NX] with row
-// pitch NX + 1. blockIdx.x = plane, blockIdx.y = field.
+// xy plane pass: the 2D transform of one (z, t) plane of one packed field. Tile [NY][NX] with row pitch
+// NX + 1. blockIdx.x = plane (ntiles = gridDim.x planes), blockIdx.y = field.
 // ---------------------------------------------------------------------------------------------
 template <typename T, int NX, int NY, bool INV, int NT>
 __global__ void __launch_bounds__(NT) k_fx_plane(T *__restrict__ data, int64_t V, FFTTables tb, const Ctrl *ctrl,
-                                                int check_active, int tkid) {
+                                                int check_active, int tkid, int ntiles) {
+  (void)ntiles;
   data += (int64_t)blockIdx.z * 4 * V * 2;
   ctrl += blockIdx.z;
   if (!should_run<T>(ctrl, check_active)) return;
@@ -142,8 +144,12 @@ __global__ void __launch_bounds__(NT) k_fx_plane(T *__restrict__ data, int64_t V
 
 // ---------------------------------------------------------------------------------------------
 // Column pass along one lattice axis of length N (z or t): a tile of N rows (row stride `rstride`
-// complex elements) by C contiguous columns, pitch C + 1. Block b covers columns
-// (b % ncb) * C .. + C of outer slice b / ncb (outer stride `ostride`).
+// complex elements) by C contiguous columns, pitch C + 1. Tile b covers columns (b % ncb) * C .. + C of
+// outer slice b / ncb (outer stride `ostride`); the pass has ntiles tiles.
+//   Where prefetch_tiles() (fft_dispatch.h) says so, blocks loop over tiles b, b + gridDim.x, ... (the
+//   planner launches one wave of blocks), and while a tile is transformed in shared memory its successor's
+//   elements are already being loaded into registers, so the global loads of one tile overlap the
+//   butterflies and the stores of the previous one. Otherwise every block takes tile blockIdx.x.
 //   MODE 0: forward (one field per block, blockIdx.y = field)
 //   MODE 1: inverse (one field per block)
 //   MODE 2: forward + filter + inverse, FPB fields per block (blockIdx.y selects the group of FPB
@@ -154,7 +160,104 @@ __global__ void __launch_bounds__(NT) k_fx_plane(T *__restrict__ data, int64_t V
 template <typename T, int N, int C, int MODE, int NT, int FPB = 4>
 __global__ void __launch_bounds__(NT) k_fx_cols(T *__restrict__ data, int64_t V, int64_t rstride, int ncb,
                                                int64_t ostride, FFTTables tb, const Ctrl *ctrl, int check_active,
-                                               int tkid, int twmu) {
+                                               int tkid, int twmu, int ntiles) {
+  if constexpr (prefetch_tiles<T, 2, MODE>()) {
+  data += (int64_t)blockIdx.z * 4 * V * 2;
+  ctrl += blockIdx.z;
+  if (!should_run<T>(ctrl, check_active)) return;
+  count_run(ctrl, tkid);
+  constexpr int P = C + 1;
+  constexpr int NF = MODE == 2 ? FPB : 1;
+  constexpr int TILE = N * P;
+  constexpr int NEL = N * C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T> *tile = reinterpret_cast<cx<T> *>(smem_raw);
+  cx<T> *tw = tile + NF * TILE;
+  __shared__ T sxyz[MODE == 2 ? C : 1];
+  __shared__ T srow[MODE == 2 ? N : 1];
+  load_twiddles<T, N>(tw, tb.tw[twmu]);
+  if constexpr (MODE == 2) {
+    for (int n = threadIdx.x; n < N; n += NT) srow[n] = convert<T>(__ldg(tb.p2part[3] + n));
+  }
+  using V2 = typename vec2<T>::type;
+  constexpr int PER = (NEL + NT - 1) / NT;
+  auto base_of = [&](int bb) { return (int64_t)(bb % ncb) * C + (int64_t)(bb / ncb) * ostride; };
+  auto field_of = [&](int f) { return MODE == 2 ? (int)blockIdx.y * FPB + f : (int)blockIdx.y; };
+  V2 reg[NF][PER];
+  auto fetch = [&](int bb) {
+    const int64_t base = base_of(bb);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      const V2 *src = reinterpret_cast<const V2 *>(data + (int64_t)field_of(f) * V * 2);
+#pragma unroll
+      for (int k = 0; k < PER; ++k) {
+        const int e = threadIdx.x + k * NT;
+        if (e < NEL) reg[f][k] = __ldg(src + base + (e / C) * rstride + (e % C));
+      }
+    }
+  };
+  constexpr bool kPrefetch = prefetch_tiles<T, 2, MODE>();
+  int b = blockIdx.x;
+  if (kPrefetch && b < ntiles) fetch(b);
+  for (; b < ntiles; b += gridDim.x) {
+    if (!kPrefetch) fetch(b);
+    const int64_t col0 = (int64_t)(b % ncb) * C;
+    const int64_t base = base_of(b);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+#pragma unroll
+      for (int k = 0; k < PER; ++k) {
+        const int e = threadIdx.x + k * NT;
+        if (e < NEL) tile[f * TILE + (e / C) * P + (e % C)] = from_vec<T>(reg[f][k]);
+      }
+    }
+    if constexpr (MODE == 2) {
+      // weight of each (row, column): w = p2max / (V (p2_xyz(column) + p2_t(row))), 0 at k = 0
+      for (int c = threadIdx.x; c < C; c += NT) {
+        const int64_t q = col0 + c;
+        const int x = (int)(q % tb.n[0]);
+        const int64_t r = q / tb.n[0];
+        const int y = (int)(r % tb.n[1]);
+        const int z = (int)(r / tb.n[1]);
+        sxyz[c] = convert<T>(__ldg(tb.p2part[0] + x) + __ldg(tb.p2part[1] + y) + __ldg(tb.p2part[2] + z));
+      }
+    }
+    __syncthreads();
+    if (kPrefetch && b + (int)gridDim.x < ntiles) fetch(b + gridDim.x);  // in flight during the transform
+    // along the rows: element stride P, pencils (columns) stride 1; the fields are stacked, TILE apart
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      if (MODE == 1) fx_axis<T, N, C, NT, true>(tile + f * TILE, tw, P, 1);
+      else fx_axis<T, N, C, NT, false>(tile + f * TILE, tw, P, 1);
+    }
+    if constexpr (MODE == 2) {
+      const T wscale = convert<T>(tb.wscale);
+      const T zero = kconst<T>(0.0);
+      for (int e = threadIdx.x; e < NEL; e += NT) {
+        const int n = e / C, c = e % C;
+        const T p2 = sxyz[c] + srow[n];
+        const T w = p2 == zero ? zero : wscale / p2;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          cx<T> &v = tile[f * TILE + n * P + c];
+          v = scale(v, w);
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int f = 0; f < NF; ++f) fx_axis<T, N, C, NT, true>(tile + f * TILE, tw, P, 1);
+    }
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      V2 *dst = reinterpret_cast<V2 *>(data + (int64_t)field_of(f) * V * 2);
+      for (int e = threadIdx.x; e < NEL; e += NT) {
+        const int n = e / C, c = e % C;
+        dst[base + n * rstride + c] = to_vec<T>(tile[f * TILE + n * P + c]);
+      }
+    }
+    __syncthreads();
+  }
+  } else {
   data += (int64_t)blockIdx.z * 4 * V * 2;
   ctrl += blockIdx.z;
   if (!should_run<T>(ctrl, check_active)) return;
@@ -236,6 +339,7 @@ __global__ void __launch_bounds__(NT) k_fx_cols(T *__restrict__ data, int64_t V,
       const int n = e / C, c = e % C;
       reinterpret_cast<typename vec2<T>::type *>(dst)[base + n * rstride + c] = to_vec<T>(tile[f * TILE + n * P + c]);
     }
+  }
   }
 }
 

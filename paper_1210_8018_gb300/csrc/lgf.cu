@@ -81,6 +81,7 @@ struct Pass {
   int kind = 0;
   int N = 0, C = 0, mode = 0, twmu = 0, ncb = 0, nblocks = 0;
   int64_t rstride = 0, ostride = 0;
+  int grid_x = 0;  // blocks launched along x: one wave of the GPU (each block loops over its tiles), or nblocks
 };
 constexpr int kFixedThreads = 256;
 bool fixed_len(int n) { return n == 8 || n == 16 || n == 24 || n == 32 || n == 48 || n == 64; }
@@ -144,6 +145,8 @@ struct lgf_ctx {
   bool residual = true;      // mixed: residual stage after the handover (LGF_RESIDUAL=0: double iterations)
   bool resid_off = false;    // this load: a rebuild made no progress, the double stage continues
   bool handover_fp64 = false;  // mixed handover transform in FP64 instead of 61-bit fixed point
+  int num_sms = 1;
+  bool fft_persist = true;  // specialised FFT passes as one wave of tile-looping blocks (LGF_FFT_PERSIST=0: off)
   int handover_split[2] = {2, 2};  // links per site in FP64 (even, odd warps), the rest in fixed point
   int update_split[2] = {2, 2};    // the same for the general (large-step) form of the double update
   bool reunit_fp64 = false;    // float stages: periodic projection onto SU(3) in double instead of float
@@ -445,6 +448,8 @@ template <> void fill_twiddles<df64>(std::vector<df64> &tw, int N) {
 
 // Opt the FFT kernels in to the dynamic shared memory each pass needs (the generic kernel: the
 // largest of its passes).
+// The specialised passes get one wave of blocks (resident blocks per SM x SMs, over the fields and the
+// configurations of the launch), each looping over its tiles with the next tile's loads in flight.
 template <typename T> lgf_status opt_in_smem(lgf_ctx *ctx, State<T> &S) {
   return with_fft_type<T>(ctx, [&](auto tag) -> lgf_status {
     using FT = decltype(tag);
@@ -453,6 +458,19 @@ template <typename T> lgf_status opt_in_smem(lgf_ctx *ctx, State<T> &S) {
       if (p.kind == 0) generic_max = std::max(generic_max, p.smem);
       else if (p.smem > 48 * 1024)
         CK(cudaFuncSetAttribute(fixed_kernel<FT>(p), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
+      if (p.kind != 0) {
+        int per_sm = 0;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fixed_kernel<FT>(p), p.threads, p.smem));
+        const int gy = p.kind == 2 && p.mode == 2 ? 4 / filter_fields_per_block<FT>() : 4;
+        const int64_t wave = (int64_t)std::max(per_sm, 1) * ctx->num_sms;
+        const int64_t gx = (wave + (int64_t)gy * ctx->nb - 1) / ((int64_t)gy * ctx->nb);
+        const bool prefetch = p.kind == 2 ? (p.mode == 0   ? prefetch_tiles<FT, 2, 0>()
+                                             : p.mode == 1 ? prefetch_tiles<FT, 2, 1>()
+                                                           : prefetch_tiles<FT, 2, 2>())
+                                          : prefetch_tiles<FT, 1, 0>();
+        p.grid_x = ctx->fft_persist && prefetch ? (int)std::min<int64_t>(p.nblocks, std::max<int64_t>(gx, 1))
+                                                : p.nblocks;
+      }
     }
     if (generic_max > 48 * 1024)
       CK(cudaFuncSetAttribute(fft_generic_kernel<FT>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)generic_max));
@@ -574,9 +592,14 @@ template <typename T> lgf_status launch_delta(lgf_ctx *ctx, State<T> &S, int cou
   TRY(timed_begin(ctx, kid<T>(KID_DELTA)));
   TRY(with_fft_type<T>(ctx, [&](auto tag) -> lgf_status {
     using FT = decltype(tag);
-    k_delta<T, NT, FT><<<dim3(ctx->nblocks_site, 1, ctx->nb), NT, 0, ctx->stream>>>(
-        S.U, reinterpret_cast<FT *>(S.P), ctx->partials, ctx->ctrl, ctx->L, counts_update, check_active,
-        kid<T>(KID_DELTA));
+    const dim3 grid(ctx->nblocks_site, 1, ctx->nb);
+    FT *P = reinterpret_cast<FT *>(S.P);
+    if constexpr (std::is_same<T, float>::value)
+      k_delta_f32<NT><<<grid, NT, 0, ctx->stream>>>(S.U, P, ctx->partials, ctx->ctrl, ctx->L, counts_update,
+                                                    check_active, kid<T>(KID_DELTA));
+    else
+      k_delta<T, NT, FT><<<grid, NT, 0, ctx->stream>>>(S.U, P, ctx->partials, ctx->ctrl, ctx->L, counts_update,
+                                                       check_active, kid<T>(KID_DELTA));
     CKL();
     return LGF_OK;
   }));
@@ -599,19 +622,20 @@ template <typename T> lgf_status launch_filter(lgf_ctx *ctx, State<T> &S, T *dat
       void *args[] = {&data, &V, &pd, &tb, &c, &check_active, (void *)&tk};
       CK(cudaLaunchKernel(fft_generic_kernel<FT>(), grid, dim3(p.threads), args, p.smem, ctx->stream));
     } else if (p.kind == 1) {
-      dim3 grid(p.nblocks, 4, ctx->nb);
+      dim3 grid(p.grid_x > 0 ? p.grid_x : p.nblocks, 4, ctx->nb);
       int64_t V = ctx->V;
       FFTTables tb = S.tables;
       const Ctrl *c = ctx->ctrl;
-      void *args[] = {&data, &V, &tb, &c, &check_active, (void *)&tk};
+      int nt = p.nblocks;
+      void *args[] = {&data, &V, &tb, &c, &check_active, (void *)&tk, &nt};
       CK(cudaLaunchKernel(fixed_kernel<FT>(p), grid, dim3(p.threads), args, p.smem, ctx->stream));
     } else {
-      dim3 grid(p.nblocks, p.mode == 2 ? 4 / filter_fields_per_block<FT>() : 4, ctx->nb);
+      dim3 grid(p.grid_x > 0 ? p.grid_x : p.nblocks, p.mode == 2 ? 4 / filter_fields_per_block<FT>() : 4, ctx->nb);
       int64_t V = ctx->V, rs = p.rstride, os = p.ostride;
-      int ncb = p.ncb, twmu = p.twmu;
+      int ncb = p.ncb, twmu = p.twmu, nt = p.nblocks;
       FFTTables tb = S.tables;
       const Ctrl *c = ctx->ctrl;
-      void *args[] = {&data, &V, &rs, &ncb, &os, &tb, &c, &check_active, (void *)&tk, &twmu};
+      void *args[] = {&data, &V, &rs, &ncb, &os, &tb, &c, &check_active, (void *)&tk, &twmu, &nt};
       CK(cudaLaunchKernel(fixed_kernel<FT>(p), grid, dim3(p.threads), args, p.smem, ctx->stream));
     }
     CKL();
@@ -1047,6 +1071,12 @@ static lgf_status create_ctx(const int n[4], int nb, lgf_ctx **out) {
     ctx->reunit_fp64 = rf && rf[0] == '1';
   }
   cudaDeviceGetAttribute(&ctx->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+  cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  if (ctx->num_sms < 1) ctx->num_sms = 1;
+  {
+    const char *fp = std::getenv("LGF_FFT_PERSIST");
+    ctx->fft_persist = !(fp && fp[0] == '0');
+  }
   // p^2 tables (position -> 4 sin^2(pi k / N)) and the filter scale p^2_max / V
   double p2max = 0;
   for (int mu = 0; mu < 4; ++mu) {
