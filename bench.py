@@ -389,8 +389,9 @@ def run_batch(args):
            "config": {"workload": "16 x 16^4 + 16 x 24^3x48 + 16 x 32^3x64, eps ~ U[0.4,0.7], alpha=0.08, theta<1e-15",
                       "sites": sites, "l2": "no flush: 26 GB of links per fix >> 129 MB L2"},
            "data": "synthetic", "steps": args.steps, "warmup": args.warmup}
+    schedules = [p for p in args.batch_schedules.split(",") if p]
     with lgf.Batch(shapes) as b:
-        for prec in ("mixed", "fp64"):
+        for prec in schedules:
             def run():
                 for w, u in zip(work, inputs):
                     w.copy_(u)
@@ -414,7 +415,7 @@ def run_batch(args):
                          "iters_max": max(its), "describe": b.describe()}
     # the same 48 configurations fixed one after another, each by a single-configuration context (one
     # context per shape, reused): what grouping and graph replay save, or cost, against separate fixes
-    for prec in ("mixed", "fp64"):
+    for prec in ([] if args.no_sequential else schedules):
         lats = {d: lgf.Lattice(d) for d in sorted(set(shapes))}
         for d, lat in lats.items():
             lat.set_stream(torch.cuda.current_stream())
@@ -435,7 +436,7 @@ def run_batch(args):
         for lat in lats.values():
             lat.close()
         out[prec]["sequential_single_contexts"] = {"time_to_theta_s": dt, "site_iterations_per_s": siters / dt}
-    out["value"] = out["mixed"]["site_iterations_per_s"]
+    out["value"] = out[schedules[0]]["site_iterations_per_s"]
     return out
 
 
@@ -549,6 +550,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--batch", action="store_true",
                     help="the batched ensemble: 16 each of 16^4, 24^3x48, 32^3x64, eps ~ U[0.4, 0.7]")
+    ap.add_argument("--batch-schedules", default="mixed,fp64",
+                    help="schedules of the ensemble leg, comma-separated (mixed, fp64, fp32)")
+    ap.add_argument("--no-sequential", action="store_true",
+                    help="ensemble leg: skip fixing the configurations one by one for comparison")
     ap.add_argument("--scan", action="store_true", help="site-iterations/s over 32^3 x n, n = 8..64")
     ap.add_argument("--autograd", action="store_true",
                     help="F_U[exp(i omega)] forward/backward at 24^4 and Adam over omega to theta <= 1e-10")
