@@ -243,8 +243,8 @@ def schedule_of(args):
             "handover": "theta <= %g (or when a chunk of float iterations stops lowering theta)" % args.theta_switch,
             "reprojection": "float links and accumulated transformation G projected onto SU(3) in float every 16 "
                             "float iterations",
-            "handover_links": "U = G U0 G^+(x+mu) from the saved FP64 input, in 61-bit fixed point (exact to FP64 "
-                              "rounding)",
+            "handover_links": "U = G U0 G^+(x+mu) from the saved FP64 input, two directions per site in FP64 and two in "
+                              "61-bit fixed point (both exact to FP64 rounding)",
             "final_approach": "float iterations on the residual R of U = U_h + R, then the double links rebuilt "
                               "exactly by the double update; theta < 1e-15 checked in FP64"}
 
@@ -679,12 +679,12 @@ def main():
                 "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % which}
 
     # end to end through the C ABI from pinned host buffers (H2D + fix + D2H inside the timed region):
-    # one untimed call, then three timed calls; the median is reported
+    # one untimed call, then five timed calls; the median is reported
     e2e = None
     if not args.no_e2e:
         work = torch.empty_like(host).pin_memory()
         samples = []
-        for rep in range(4):
+        for rep in range(6):
             work.copy_(host)
             barrier()
             t0 = time.perf_counter()
@@ -697,7 +697,7 @@ def main():
         nbytes = 4 * V * 144 * ws  # every rank copies its own links in and out
         e2e = {"value": work_all / dt_max, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                "time_to_theta_s": dt_max, "samples_s": [round(d, 4) for d, _ in samples],
-               "step": "one lgf_fix call on pinned host links (median of 3 timed calls after 1 untimed)"}
+               "step": "one lgf_fix call on pinned host links (median of 5 timed calls after 1 untimed)"}
 
     if rank == 0:
         gpu_launches = sum(v[0] for v in head["ktimes"].values())

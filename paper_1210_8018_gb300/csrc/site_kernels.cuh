@@ -796,17 +796,28 @@ __global__ void k_aos_to_planes(const double *__restrict__ A, T *__restrict__ Pl
 }
 
 template <typename T>
-__global__ void k_planes_to_aos(const T *__restrict__ Pl, double *__restrict__ A, int64_t V, int nmat, int np,
-                                int64_t idx0, int64_t n) {
-  const int64_t idx = idx0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= idx0 + n || idx >= (int64_t)nmat * V) return;
-  const int64_t m = idx / V, s = idx - m * V;
-  double2 *dst = reinterpret_cast<double2 *>(A) + idx * 9;
-  m3<T> u;
-  for (int e = 0; e < np; ++e) u.e[e] = ld(Pl, (m * np + e) * V + s);
-  if (np == 6) complete_row2(u);
+__global__ void __launch_bounds__(256) k_planes_to_aos(const T *__restrict__ Pl, double *__restrict__ A, int64_t V,
+                                                       int nmat, int np, int64_t idx0, int64_t n) {
+  // Each thread forms one matrix from the planes (coalesced loads) into shared memory; the block then
+  // writes its matrices' contiguous 144-byte records with consecutive threads on consecutive 16-byte
+  // chunks (a thread writing its own record would put every store instruction's 32 chunks 144 bytes apart).
+  constexpr int NTB = 256;
+  __shared__ double2 rec[NTB * 9];
+  const int64_t first = idx0 + (int64_t)blockIdx.x * NTB;
+  const int64_t end = min(idx0 + n, (int64_t)nmat * V);
+  const int cnt = (int)max((int64_t)0, min((int64_t)NTB, end - first));
+  const int64_t idx = first + threadIdx.x;
+  if (threadIdx.x < cnt) {
+    const int64_t m = idx / V, s = idx - m * V;
+    m3<T> u;
+    for (int e = 0; e < np; ++e) u.e[e] = ld(Pl, (m * np + e) * V + s);
+    if (np == 6) complete_row2(u);
 #pragma unroll
-  for (int e = 0; e < 9; ++e) dst[e] = make_double2((double)u.e[e].r, (double)u.e[e].i);
+    for (int e = 0; e < 9; ++e) rec[threadIdx.x * 9 + e] = make_double2((double)u.e[e].r, (double)u.e[e].i);
+  }
+  __syncthreads();
+  double2 *dst = reinterpret_cast<double2 *>(A) + first * 9;
+  for (int q = threadIdx.x; q < cnt * 9; q += NTB) dst[q] = rec[q];
 }
 
 // Full site matrices (AoS double) <-> packed anti-Hermitian traceless fields (planes of PT).
