@@ -146,7 +146,8 @@ struct lgf_ctx {
   bool resid_off = false;    // this load: a rebuild made no progress, the double stage continues
   bool handover_fp64 = false;  // mixed handover transform in FP64 instead of 61-bit fixed point
   int num_sms = 1;
-  bool fft_persist = true;  // specialised FFT passes as one wave of tile-looping blocks (LGF_FFT_PERSIST=0: off)
+  bool fft_persist = true;   // specialised FFT passes as one wave of tile-looping blocks (LGF_FFT_PERSIST=0: off)
+  bool update_twalk = true;  // float update walking along t over chunks of 8 slices (LGF_UPDATE_TWALK=0: off)
   int handover_split[2] = {2, 2};  // links per site in FP64 (even, odd warps), the rest in fixed point
   int update_split[2] = {2, 2};    // the same for the general (large-step) form of the double update
   bool reunit_fp64 = false;    // float stages: periodic projection onto SU(3) in double instead of float
@@ -711,7 +712,19 @@ lgf_status launch_iteration_float(lgf_ctx *ctx, double alpha, bool reunit) {
   TRY(timed_begin(ctx, kidx));
   const dim3 grid(grid1(ctx->V, NT), 1, ctx->nb);
   const float ha = (float)(0.5 * alpha);
-  if (reunit && ctx->reunit_fp64)
+  auto walk = [&](auto tch) {
+    constexpr int TCH = decltype(tch)::value;
+    const dim3 gtw(grid1(ctx->L.stride[3], NT), ctx->n[3] / TCH, ctx->nb);
+    if (reunit && ctx->reunit_fp64)
+      k_update_fused_f32_tw<NT, 2, TCH><<<gtw, NT, 0, ctx->stream>>>(S.U, S.P, ctx->Gacc, ha, ctx->L, ctx->ctrl, kidx);
+    else if (reunit)
+      k_update_fused_f32_tw<NT, 1, TCH><<<gtw, NT, 0, ctx->stream>>>(S.U, S.P, ctx->Gacc, ha, ctx->L, ctx->ctrl, kidx);
+    else
+      k_update_fused_f32_tw<NT, 0, TCH><<<gtw, NT, 0, ctx->stream>>>(S.U, S.P, ctx->Gacc, ha, ctx->L, ctx->ctrl, kidx);
+  };
+  if (ctx->update_twalk && ctx->n[3] % 8 == 0) {
+    walk(std::integral_constant<int, 8>());
+  } else if (reunit && ctx->reunit_fp64)
     k_update_fused_f32<NT, 2><<<grid, NT, 0, ctx->stream>>>(S.U, S.P, ctx->Gacc, ha, ctx->L, ctx->ctrl, kidx);
   else if (reunit)
     k_update_fused_f32<NT, 1><<<grid, NT, 0, ctx->stream>>>(S.U, S.P, ctx->Gacc, ha, ctx->L, ctx->ctrl, kidx);
@@ -1076,6 +1089,8 @@ static lgf_status create_ctx(const int n[4], int nb, lgf_ctx **out) {
   {
     const char *fp = std::getenv("LGF_FFT_PERSIST");
     ctx->fft_persist = !(fp && fp[0] == '0');
+    const char *tw = std::getenv("LGF_UPDATE_TWALK");
+    ctx->update_twalk = !(tw && tw[0] == '0');
   }
   // p^2 tables (position -> 4 sin^2(pi k / N)) and the filter scale p^2_max / V
   double p2max = 0;

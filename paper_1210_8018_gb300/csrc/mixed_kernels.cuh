@@ -79,6 +79,72 @@ __global__ void __launch_bounds__(NT) k_update_fused_f32(float *__restrict__ U, 
   }
 }
 
+// The same update walking along t: thread (x, y, z) takes the TCH consecutive t-slices of chunk blockIdx.y
+// one after another. The g(x + t) it forms for the links U_t is the g(x) of its next slice, kept in
+// registers: every t-neighbour's Delta-tilde is read and projected once instead of twice (in site order the
+// second read comes a whole 3D slice later, after about 140 MB of other traffic at 64^4, and misses the L2).
+// Same arithmetic per site as k_update_fused_f32 (measured at 64^4: 1.47 -> 1.37 ms). Needs Nt % TCH == 0.
+template <int NT, int REUNIT, int TCH>
+__global__ void __launch_bounds__(NT) k_update_fused_f32_tw(float *__restrict__ U, const float *__restrict__ P,
+                                                           float *__restrict__ Gacc, float half_alpha, Lattice L,
+                                                           const Ctrl *ctrl, int tkid) {
+  const int64_t V = L.V;
+  {
+    const int cfg = blockIdx.z;
+    U += (int64_t)cfg * 4 * link_plane_stride<float>(V);
+    P += (int64_t)cfg * 4 * V * 2;
+    Gacc += (int64_t)cfg * 6 * V * 2;
+    ctrl += cfg;
+  }
+  if (!stage_active<float>(ctrl)) return;
+  count_run(ctrl, tkid);
+  const int64_t nxyz = L.stride[3];
+  const int64_t q = (int64_t)blockIdx.x * NT + threadIdx.x;
+  if (q >= nxyz) return;
+  const int t0 = blockIdx.y * TCH;
+  int c[4];
+  site_coords(L, q + (int64_t)t0 * nxyz, c);
+  // U_mu(x) <- g(x) U_mu(x) g(y)^dagger, projected like the float links
+  auto link_update = [&](float *plane, int64_t s, const m3<float> &gx, const m3<float> &gy) {
+    m3<float> u, tm;
+    load_link(plane, V, s, u);
+    mul_rows01(gx, u, tm);
+    mul_adj_rows01(tm, gy, u);
+    if constexpr (REUNIT == 1) reunitarize(u);
+    if constexpr (REUNIT == 2) reunitarize_fp64(u);
+    store_link(plane, V, s, u);
+  };
+  m3<float> gx;
+  gauge_from_packed(P, V, q + (int64_t)t0 * nxyz, half_alpha, gx);
+#pragma unroll 1
+  for (int k = 0; k < TCH; ++k) {
+    const int t = t0 + k;
+    const int64_t s = q + (int64_t)t * nxyz;
+    {
+      m3<float> a, tm;
+      // G(x) <- g(x) G(x), stored as rows 0 and 1 (like the float links)
+#pragma unroll
+      for (int e = 0; e < 6; ++e) a.e[e] = ld(Gacc, (int64_t)e * V + s);
+      complete_row2(a);
+      mul_rows01(gx, a, tm);
+      if constexpr (REUNIT == 1) reunitarize(tm);
+      if constexpr (REUNIT == 2) reunitarize_fp64(tm);
+#pragma unroll
+      for (int e = 0; e < 6; ++e) st(Gacc, (int64_t)e * V + s, tm.e[e]);
+    }
+#pragma unroll 1
+    for (int mu = 0; mu < 3; ++mu) {
+      m3<float> gy;
+      gauge_from_packed(P, V, site_fwd(L, s, mu, c[mu]), half_alpha, gy);
+      link_update(U + (int64_t)mu * link_plane_stride<float>(V), s, gx, gy);
+    }
+    m3<float> gt;  // g(x + t), the g(x) of the next slice
+    gauge_from_packed(P, V, q + (int64_t)(t + 1 == L.n[3] ? 0 : t + 1) * nxyz, half_alpha, gt);
+    link_update(U + (int64_t)3 * link_plane_stride<float>(V), s, gx, gt);
+    gx = gt;
+  }
+}
+
 // Float links (rows 0 and 1, 6 planes per direction) from the double link planes (9 per direction),
 // rounded to nearest.
 __global__ void k_narrow_link_planes(const double *__restrict__ U64, float *__restrict__ U32, int64_t V, int64_t idx0,
