@@ -42,7 +42,7 @@ FP64_FLOP_PER_CLK = 152 * 2 * 2      # 152 SMs x 2 DFMA per clock x 2 flop
 FP32_OPS_PER_CLK = 152 * 128         # 152 SMs x 128 FP32 lanes (one FADD, FMUL or FFMA each per clock)
 # DRAM bytes (read + write) per launch of a kernel at 64^4, from one ncu capture of
 # dram__bytes_read.sum + dram__bytes_write.sum; valid only for the kernel versions that were captured.
-TRAFFIC_64 = {"gauge_update_fused.f32": 4.84e9 + 4.35e9, "update_residual.f32": 10.29e9 + 6.11e9}
+TRAFFIC_64 = {"gauge_update_fused.f32": 4.79e9 + 4.11e9, "update_residual.f32": 9.96e9 + 6.25e9}
 
 
 def peaks():

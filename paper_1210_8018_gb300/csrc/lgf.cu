@@ -147,7 +147,7 @@ struct lgf_ctx {
   bool handover_fp64 = false;  // mixed handover transform in FP64 instead of 61-bit fixed point
   int num_sms = 1;
   bool fft_persist = true;   // specialised FFT passes as one wave of tile-looping blocks (LGF_FFT_PERSIST=0: off)
-  bool update_twalk = true;  // float update walking along t over chunks of 8 slices (LGF_UPDATE_TWALK=0: off)
+  bool update_twalk = true;  // float and residual updates walking along t over chunks of 8 slices (LGF_UPDATE_TWALK=0: off)
   int handover_split[2] = {2, 2};  // links per site in FP64 (even, odd warps), the rest in fixed point
   int update_split[2] = {2, 2};    // the same for the general (large-step) form of the double update
   bool reunit_fp64 = false;    // float stages: periodic projection onto SU(3) in double instead of float
@@ -820,9 +820,14 @@ lgf_status residual_begin(lgf_ctx *ctx) {
 lgf_status launch_iteration_residual(lgf_ctx *ctx, double alpha) {
   TRY(launch_filter<float>(ctx, ctx->s32, ctx->s32.P, 3));
   TRY(timed_begin(ctx, kid<float>(KID_UPDATE_RESIDUAL)));
-  k_update_residual<NT><<<dim3(grid1(ctx->V, NT), 1, ctx->nb), NT, 0, ctx->stream>>>(ctx->s32.U, ctx->Rres, ctx->Kres, ctx->s32.P,
-                                                                 (float)(0.5 * alpha), ctx->L, ctx->ctrl,
-                                                                 kid<float>(KID_UPDATE_RESIDUAL));
+  if (ctx->update_twalk && ctx->n[3] % 8 == 0)
+    k_update_residual_tw<NT, 8><<<dim3(grid1(ctx->L.stride[3], NT), ctx->n[3] / 8, ctx->nb), NT, 0, ctx->stream>>>(
+        ctx->s32.U, ctx->Rres, ctx->Kres, ctx->s32.P, (float)(0.5 * alpha), ctx->L, ctx->ctrl,
+        kid<float>(KID_UPDATE_RESIDUAL));
+  else
+    k_update_residual<NT><<<dim3(grid1(ctx->V, NT), 1, ctx->nb), NT, 0, ctx->stream>>>(
+        ctx->s32.U, ctx->Rres, ctx->Kres, ctx->s32.P, (float)(0.5 * alpha), ctx->L, ctx->ctrl,
+        kid<float>(KID_UPDATE_RESIDUAL));
   CKL();
   TRY(timed_end(ctx));
   return launch_delta_residual(ctx, 1);

@@ -480,6 +480,80 @@ __global__ void __launch_bounds__(NT) k_update_residual(const float *__restrict_
   }
 }
 
+// The same residual update walking along t (as k_update_fused_f32_tw): thread (x, y, z) takes the TCH
+// t-slices of chunk blockIdx.y, and the b formed for its links U_t is the a of its next slice, so each
+// t-neighbour's Delta-tilde is read and projected once. Same arithmetic per site. Needs Nt % TCH == 0.
+template <int NT, int TCH>
+__global__ void __launch_bounds__(NT, 2) k_update_residual_tw(const float *__restrict__ B, float *__restrict__ R,
+                                                          float *__restrict__ K, const float *__restrict__ P,
+                                                          float half_alpha, Lattice L, const Ctrl *ctrl, int tkid) {
+  const int64_t V = L.V;
+  {
+    const int cfg = blockIdx.z;
+    B += (int64_t)cfg * 4 * link_plane_stride<float>(V);
+    R += (int64_t)cfg * 36 * V * 2;
+    K += (int64_t)cfg * 9 * V * 2;
+    P += (int64_t)cfg * 4 * V * 2;
+    ctrl += cfg;
+  }
+  if (!residual_active(ctrl)) return;
+  count_run(ctrl, tkid);
+  const int64_t nxyz = L.stride[3];
+  const int64_t q = (int64_t)blockIdx.x * NT + threadIdx.x;
+  if (q >= nxyz) return;
+  const int t0 = blockIdx.y * TCH;
+  int c[4];
+  site_coords(L, q + (int64_t)t0 * nxyz, c);
+  // R_mu(x) <- R_mu(x) + a U + (U + a U) b^+ with U = B + R
+  auto link_update = [&](int mu, int64_t s, const m3<float> &a, const m3<float> &b) {
+    m3<float> u, r, w, t;
+    float *rp = R + (int64_t)mu * 18 * V;
+    load9(rp, V, s, r);
+    load_link(B + (int64_t)mu * link_plane_stride<float>(V), V, s, u);
+#pragma unroll
+    for (int e = 0; e < 9; ++e) u.e[e] = u.e[e] + r.e[e];
+    mul(a, u, t);  // a U
+#pragma unroll
+    for (int e = 0; e < 9; ++e) w.e[e] = u.e[e] + t.e[e];  // g U
+    mul_adj(w, b, u);                                      // (g U) b^+
+#pragma unroll
+    for (int e = 0; e < 9; ++e) st(rp, (int64_t)e * V + s, r.e[e] + (t.e[e] + u.e[e]));
+  };
+  m3<float> a;
+  {
+    m3<float> X;
+    unpack_scaled(P, V, q + (int64_t)t0 * nxyz, half_alpha, X);
+    residual_step(X, a);
+  }
+#pragma unroll 1
+  for (int k = 0; k < TCH; ++k) {
+    const int t = t0 + k;
+    const int64_t s = q + (int64_t)t * nxyz;
+    {
+      m3<float> kk, tm;
+      load9(K, V, s, kk);
+      mul(a, kk, tm);
+#pragma unroll
+      for (int e = 0; e < 9; ++e) st(K, (int64_t)e * V + s, (a.e[e] + kk.e[e]) + tm.e[e]);
+    }
+#pragma unroll 1
+    for (int mu = 0; mu < 3; ++mu) {
+      m3<float> X, b;
+      unpack_scaled(P, V, site_fwd(L, s, mu, c[mu]), half_alpha, X);
+      residual_step(X, b);
+      link_update(mu, s, a, b);
+    }
+    m3<float> bt;  // b of the link U_t: the a of the next slice
+    {
+      m3<float> X;
+      unpack_scaled(P, V, q + (int64_t)(t + 1 == L.n[3] ? 0 : t + 1) * nxyz, half_alpha, X);
+      residual_step(X, bt);
+    }
+    link_update(3, s, a, bt);
+    a = bt;
+  }
+}
+
 // H = proj(1 + K) into G (double) and a = H - 1 in double-float into A: the gauge field with which the
 // double update (small-step form) rebuilds U_h -> H U_h H^+(x + mu). K is the transformation gathered in the
 // residual stage, of the size of the remaining gauge rotation (about 1e-4): per warp, when every |K_ij| of
