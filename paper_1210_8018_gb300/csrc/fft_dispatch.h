@@ -9,7 +9,9 @@
 namespace lgf {
 
 // Specialised pass (fft_fixed.cuh): kind 1 = xy plane (mode 0 forward, 1 inverse), kind 2 = columns
-// (mode 0 forward, 1 inverse, 2 forward + filter + inverse) with C in {16, 32}; N in {8,16,24,32,48,64}.
+// (mode 0 forward, 1 inverse, 2 forward + filter + inverse) with C in {16, 32}; N in {8,16,24,32,48,64};
+// kind 3 = the float column pass with the filter held in registers (k_fx_tfilter64: N = 64, C = 32, mode 2);
+// kind 4 = the float 64 x 64 xy plane pass held in registers (k_fx_plane64; mode 0 forward, 1 inverse).
 template <typename FT> const void *fft_fixed_kernel(int kind, int mode, int N, int C);
 // Generic pass (fft.cuh, k_fft_pass).
 template <typename FT> const void *fft_generic_kernel();

@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <array>
+#include <functional>
 #include <map>
 #include <cmath>
 #include <cstdio>
@@ -147,6 +148,8 @@ struct lgf_ctx {
   bool handover_fp64 = false;  // mixed handover transform in FP64 instead of 61-bit fixed point
   int num_sms = 1;
   bool fft_persist = true;   // specialised FFT passes as one wave of tile-looping blocks (LGF_FFT_PERSIST=0: off)
+  bool tfilter_reg = true;   // float t pass with the filter in registers at Nt = 64 (LGF_TFILTER_REG=0: off)
+  bool xy_reg = true;        // float 64 x 64 xy passes in registers (LGF_XY_REG=0: off)
   bool update_twalk = true;  // float and residual updates walking along t over chunks of 8 slices (LGF_UPDATE_TWALK=0: off)
   int handover_split[2] = {2, 2};  // links per site in FP64 (even, odd warps), the rest in fixed point
   int update_split[2] = {2, 2};    // the same for the general (large-step) form of the double update
@@ -298,7 +301,7 @@ template <typename T> bool plan_fixed(lgf_ctx *ctx, State<T> &S) {
   const size_t es = sizeof(cx<T>);
   // filter_fields_per_block<FT>() of the FFT type FT of this state
   const int fields_per_filter_block = (sizeof(T) == 8 && !ctx->fft_df64) ? filter_fields_per_block<double>() : 1;
-  auto plane = [&](int mode, int kid) {
+  std::function<Pass(int, int)> plane = [&](int mode, int kid) {
     Pass p{};
     p.kind = 1;
     p.N = Nx;
@@ -325,10 +328,25 @@ template <typename T> bool plan_fixed(lgf_ctx *ctx, State<T> &S) {
     p.smem = (size_t)((mode == 2 ? fields_per_filter_block : 1) * N * (C + 1) + N) * es;
     return p;
   };
+  if (sizeof(T) == 4 && Nx == 64 && ctx->xy_reg) {
+    auto plane_reg = plane;  // the register form of the 64 x 64 plane pass (512 threads, static shared memory)
+    plane = [plane_reg](int mode, int kid) {
+      Pass p = plane_reg(mode, kid);
+      p.kind = 4;
+      p.threads = 512;
+      p.smem = 0;
+      return p;
+    };
+  }
   S.passes.clear();
   S.passes.push_back(plane(0, KID_FFT_XY_FWD));
   S.passes.push_back(cols(Nz, 0, Nxy, (int)(Nxy / C), Nxyz, Nt, 2, KID_FFT_Z_FWD));
   S.passes.push_back(cols(Nt, 2, Nxyz, (int)(Nxyz / C), 0, 1, 3, KID_FFT_T_FILTER));
+  if (sizeof(T) == 4 && Nt == 64 && C == 32 && ctx->tfilter_reg) {
+    Pass &p = S.passes.back();  // the register form of the same pass (static shared memory)
+    p.kind = 3;
+    p.smem = 0;
+  }
   S.passes.push_back(cols(Nz, 1, Nxy, (int)(Nxy / C), Nxyz, Nt, 2, KID_FFT_Z_INV));
   S.passes.push_back(plane(1, KID_FFT_XY_INV));
   return true;
@@ -468,7 +486,7 @@ template <typename T> lgf_status opt_in_smem(lgf_ctx *ctx, State<T> &S) {
         const bool prefetch = p.kind == 2 ? (p.mode == 0   ? prefetch_tiles<FT, 2, 0>()
                                              : p.mode == 1 ? prefetch_tiles<FT, 2, 1>()
                                                            : prefetch_tiles<FT, 2, 2>())
-                                          : prefetch_tiles<FT, 1, 0>();
+                                          : prefetch_tiles<FT, 1, 0>();  // kind 1 and 3: one tile per block
         p.grid_x = ctx->fft_persist && prefetch ? (int)std::min<int64_t>(p.nblocks, std::max<int64_t>(gx, 1))
                                                 : p.nblocks;
       }
@@ -622,7 +640,7 @@ template <typename T> lgf_status launch_filter(lgf_ctx *ctx, State<T> &S, T *dat
       const Ctrl *c = ctx->ctrl;
       void *args[] = {&data, &V, &pd, &tb, &c, &check_active, (void *)&tk};
       CK(cudaLaunchKernel(fft_generic_kernel<FT>(), grid, dim3(p.threads), args, p.smem, ctx->stream));
-    } else if (p.kind == 1) {
+    } else if (p.kind == 1 || p.kind == 4) {
       dim3 grid(p.grid_x > 0 ? p.grid_x : p.nblocks, 4, ctx->nb);
       int64_t V = ctx->V;
       FFTTables tb = S.tables;
@@ -1094,6 +1112,10 @@ static lgf_status create_ctx(const int n[4], int nb, lgf_ctx **out) {
   {
     const char *fp = std::getenv("LGF_FFT_PERSIST");
     ctx->fft_persist = !(fp && fp[0] == '0');
+    const char *tr = std::getenv("LGF_TFILTER_REG");
+    ctx->tfilter_reg = !(tr && tr[0] == '0');
+    const char *xr = std::getenv("LGF_XY_REG");
+    ctx->xy_reg = !(xr && xr[0] == '0');
     const char *tw = std::getenv("LGF_UPDATE_TWALK");
     ctx->update_twalk = !(tw && tw[0] == '0');
   }

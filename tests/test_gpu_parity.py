@@ -73,6 +73,43 @@ def test_fourier_filter_generic_passes(lgf, dims, monkeypatch):
     assert_matrix_close(out32, Dt_ref, rtol=5e-6, scale=float(np.abs(Dt_ref).max()))
 
 
+@pytest.mark.parametrize("dims", [(8, 8, 8, 64), (16, 16, 32, 64)])
+def test_float_t_filter_in_registers(lgf, dims, monkeypatch):
+    """The float t pass with the filter held in registers (Nt = 64) applies the operations of the
+    shared-memory tile pass in the same order: the filtered field is the same bits (LGF_TFILTER_REG=0 selects
+    the tile pass), and it matches the oracle's filter to float accuracy."""
+    U = synth.config(dims, 26, 0.6)
+    D = oracle.delta(U)
+    Dt_ref = oracle.fourier_filter(D)
+    outs = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("LGF_TFILTER_REG", flag)
+        with lgf.Lattice(dims) as lat:
+            out = np.empty_like(D)
+            lat.filter(D, out, "fp32")
+        outs.append(out)
+    assert np.array_equal(outs[0], outs[1])
+    assert_matrix_close(outs[0], Dt_ref, rtol=5e-6, scale=float(np.abs(Dt_ref).max()))
+
+
+def test_float_xy_planes_in_registers(lgf, monkeypatch):
+    """The float 64 x 64 xy passes held in registers apply the operations of the shared-memory tile passes
+    in the same order: the filtered field is the same bits as with LGF_XY_REG=0, and matches the oracle."""
+    dims = (64, 64, 8, 8)
+    U = synth.config(dims, 27, 0.6)
+    D = oracle.delta(U)
+    Dt_ref = oracle.fourier_filter(D)
+    outs = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("LGF_XY_REG", flag)
+        with lgf.Lattice(dims) as lat:
+            out = np.empty_like(D)
+            lat.filter(D, out, "fp32")
+        outs.append(out)
+    assert np.array_equal(outs[0], outs[1])
+    assert_matrix_close(outs[0], Dt_ref, rtol=5e-6, scale=float(np.abs(Dt_ref).max()))
+
+
 @pytest.mark.parametrize("dims", DIMS)
 def test_gauge_field(lgf, dims):
     U = synth.config(dims, 23, 0.6)
