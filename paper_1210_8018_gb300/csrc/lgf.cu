@@ -150,7 +150,7 @@ struct lgf_ctx {
   bool fft_persist = true;   // specialised FFT passes as one wave of tile-looping blocks (LGF_FFT_PERSIST=0: off)
   bool tfilter_reg = true;   // float t pass with the filter in registers at Nt = 64 (LGF_TFILTER_REG=0: off)
   bool xy_reg = true;        // float 64 x 64 xy passes in registers (LGF_XY_REG=0: off)
-  bool update_twalk = true;  // float and residual updates walking along t over chunks of 8 slices (LGF_UPDATE_TWALK=0: off)
+  bool twalk = true;  // float and residual Delta and updates walking along t, 8 slices per thread (LGF_TWALK=0: off)
   int handover_split[2] = {2, 2};  // links per site in FP64 (even, odd warps), the rest in fixed point
   int update_split[2] = {2, 2};    // the same for the general (large-step) form of the double update
   bool reunit_fp64 = false;    // float stages: periodic projection onto SU(3) in double instead of float
@@ -613,9 +613,14 @@ template <typename T> lgf_status launch_delta(lgf_ctx *ctx, State<T> &S, int cou
     using FT = decltype(tag);
     const dim3 grid(ctx->nblocks_site, 1, ctx->nb);
     FT *P = reinterpret_cast<FT *>(S.P);
-    if constexpr (std::is_same<T, float>::value)
-      k_delta_f32<NT><<<grid, NT, 0, ctx->stream>>>(S.U, P, ctx->partials, ctx->ctrl, ctx->L, counts_update,
-                                                    check_active, kid<T>(KID_DELTA));
+    if constexpr (std::is_same<T, float>::value) {
+      if (ctx->twalk && ctx->n[3] % 8 == 0)
+        k_delta_f32_tw<NT, 8><<<dim3(grid1(ctx->L.stride[3], NT), ctx->n[3] / 8, ctx->nb), NT, 0, ctx->stream>>>(
+            S.U, P, ctx->partials, ctx->ctrl, ctx->L, counts_update, check_active, kid<T>(KID_DELTA));
+      else
+        k_delta_f32<NT><<<grid, NT, 0, ctx->stream>>>(S.U, P, ctx->partials, ctx->ctrl, ctx->L, counts_update,
+                                                      check_active, kid<T>(KID_DELTA));
+    }
     else
       k_delta<T, NT, FT><<<grid, NT, 0, ctx->stream>>>(S.U, P, ctx->partials, ctx->ctrl, ctx->L, counts_update,
                                                        check_active, kid<T>(KID_DELTA));
@@ -740,7 +745,7 @@ lgf_status launch_iteration_float(lgf_ctx *ctx, double alpha, bool reunit) {
     else
       k_update_fused_f32_tw<NT, 0, TCH><<<gtw, NT, 0, ctx->stream>>>(S.U, S.P, ctx->Gacc, ha, ctx->L, ctx->ctrl, kidx);
   };
-  if (ctx->update_twalk && ctx->n[3] % 8 == 0) {
+  if (ctx->twalk && ctx->n[3] % 8 == 0) {
     walk(std::integral_constant<int, 8>());
   } else if (reunit && ctx->reunit_fp64)
     k_update_fused_f32<NT, 2><<<grid, NT, 0, ctx->stream>>>(S.U, S.P, ctx->Gacc, ha, ctx->L, ctx->ctrl, kidx);
@@ -800,9 +805,14 @@ lgf_status launch_delta_residual(lgf_ctx *ctx, int counts_update) {
   TRY(timed_begin(ctx, kid<float>(KID_DELTA_RESIDUAL)));
   TRY(with_fft_type<double>(ctx, [&](auto tag) -> lgf_status {
     using FT = decltype(tag);
-    k_delta_residual<NT, FT><<<dim3(ctx->nblocks_site, 1, ctx->nb), NT, 0, ctx->stream>>>(
-        ctx->Rres, reinterpret_cast<const FT *>(ctx->s64.P), ctx->s32.P, ctx->partials, ctx->ctrl, ctx->L,
-        counts_update, kid<float>(KID_DELTA_RESIDUAL));
+    if (ctx->twalk && ctx->n[3] % 8 == 0)
+      k_delta_residual_tw<NT, FT, 8><<<dim3(grid1(ctx->L.stride[3], NT), ctx->n[3] / 8, ctx->nb), NT, 0, ctx->stream>>>(
+          ctx->Rres, reinterpret_cast<const FT *>(ctx->s64.P), ctx->s32.P, ctx->partials, ctx->ctrl, ctx->L,
+          counts_update, kid<float>(KID_DELTA_RESIDUAL));
+    else
+      k_delta_residual<NT, FT><<<dim3(ctx->nblocks_site, 1, ctx->nb), NT, 0, ctx->stream>>>(
+          ctx->Rres, reinterpret_cast<const FT *>(ctx->s64.P), ctx->s32.P, ctx->partials, ctx->ctrl, ctx->L,
+          counts_update, kid<float>(KID_DELTA_RESIDUAL));
     CKL();
     return LGF_OK;
   }));
@@ -838,7 +848,7 @@ lgf_status residual_begin(lgf_ctx *ctx) {
 lgf_status launch_iteration_residual(lgf_ctx *ctx, double alpha) {
   TRY(launch_filter<float>(ctx, ctx->s32, ctx->s32.P, 3));
   TRY(timed_begin(ctx, kid<float>(KID_UPDATE_RESIDUAL)));
-  if (ctx->update_twalk && ctx->n[3] % 8 == 0)
+  if (ctx->twalk && ctx->n[3] % 8 == 0)
     k_update_residual_tw<NT, 8><<<dim3(grid1(ctx->L.stride[3], NT), ctx->n[3] / 8, ctx->nb), NT, 0, ctx->stream>>>(
         ctx->s32.U, ctx->Rres, ctx->Kres, ctx->s32.P, (float)(0.5 * alpha), ctx->L, ctx->ctrl,
         kid<float>(KID_UPDATE_RESIDUAL));
@@ -1116,8 +1126,8 @@ static lgf_status create_ctx(const int n[4], int nb, lgf_ctx **out) {
     ctx->tfilter_reg = !(tr && tr[0] == '0');
     const char *xr = std::getenv("LGF_XY_REG");
     ctx->xy_reg = !(xr && xr[0] == '0');
-    const char *tw = std::getenv("LGF_UPDATE_TWALK");
-    ctx->update_twalk = !(tw && tw[0] == '0');
+    const char *tw = std::getenv("LGF_TWALK");
+    ctx->twalk = !(tw && tw[0] == '0');
   }
   // p^2 tables (position -> 4 sin^2(pi k / N)) and the filter scale p^2_max / V
   double p2max = 0;

@@ -399,6 +399,91 @@ __global__ void __launch_bounds__(NT, 4) k_delta_residual(const float *__restric
   reduce_and_finalize<NT>(th, f, partials, ctrl, V, counts_update, ctrl->f_base);
 }
 
+// The same residual Delta walking along t (as k_delta_f32_tw): the combinations of R_t(x) accumulated
+// for one slice are those of the backward link R_t(x - t) of the next, kept in registers, so seven
+// residual links are read per site instead of eight. Same sums in the same order (Delta the same bits).
+// Needs Nt % TCH == 0.
+template <int NT, typename PT, int TCH>
+__global__ void __launch_bounds__(NT, 4) k_delta_residual_tw(const float *__restrict__ R, const PT *__restrict__ Ph,
+                                                         float *__restrict__ P, double *partials, Ctrl *ctrl,
+                                                         Lattice L, int counts_update, int tkid) {
+  const int64_t V = L.V;
+  const unsigned nblk = gridDim.x * gridDim.y;
+  {
+    const int cfg = blockIdx.z;
+    R += (int64_t)cfg * 36 * V * 2;
+    Ph += (int64_t)cfg * 4 * V * 2;
+    P += (int64_t)cfg * 4 * V * 2;
+    partials += (int64_t)cfg * 2 * nblk;
+    ctrl += cfg;
+  }
+  if (!residual_active(ctrl)) return;
+  count_run(ctrl, tkid);
+  const int64_t nxyz = L.stride[3];
+  const int64_t q = (int64_t)blockIdx.x * NT + threadIdx.x;
+  double th = 0.0, f = 0.0;
+  if (q < nxyz) {
+    const int t0 = blockIdx.y * TCH;
+    int c[4];
+    site_coords(L, q + (int64_t)t0 * nxyz, c);
+    const float *plane_t = R + (int64_t)3 * 18 * V;
+    float tb[9];  // combinations of R_t(x - t): the previous slice's R_t(x)
+    {
+      m3<float> u;
+      load9(plane_t, V, site_back(L, q + (int64_t)t0 * nxyz, 3, t0), u);
+#pragma unroll
+      for (int e = 0; e < 9; ++e) tb[e] = 0.f;
+      accumulate_link(u, 1.f, tb);
+    }
+#pragma unroll 1
+    for (int k = 0; k < TCH; ++k) {
+      const int64_t s = q + (int64_t)(t0 + k) * nxyz;
+      float acc[9];
+#pragma unroll
+      for (int e = 0; e < 9; ++e) acc[e] = 0.f;
+      float fs = 0.f;
+#pragma unroll
+      for (int mu = 0; mu < 3; ++mu) {
+        const float *plane = R + (int64_t)mu * 18 * V;
+        m3<float> u;
+        load9(plane, V, site_back(L, s, mu, c[mu]), u);  // R_mu(x - mu)
+        accumulate_link(u, 1.f, acc);
+        load9(plane, V, s, u);  // - R_mu(x)
+        accumulate_link(u, -1.f, acc);
+        fs += u.e[0].r + u.e[4].r + u.e[8].r;
+      }
+      {
+        m3<float> u;
+        load9(plane_t, V, s, u);
+#pragma unroll
+        for (int e = 0; e < 9; ++e) acc[e] = fmaf(1.f, tb[e], acc[e]);  // + R_t(x - t)
+        accumulate_link(u, -1.f, acc);                                   // - R_t(x)
+        fs += u.e[0].r + u.e[4].r + u.e[8].r;
+#pragma unroll
+        for (int e = 0; e < 9; ++e) tb[e] = 0.f;
+        accumulate_link(u, 1.f, tb);
+      }
+      const float m = (acc[6] + acc[7] + acc[8]) / 3.f;
+      float d[8] = {acc[0], acc[1], acc[2], acc[3], acc[4], acc[5], 2.f * (acc[6] - m), 2.f * (acc[7] - m)};
+#pragma unroll
+      for (int qq = 0; qq < 4; ++qq) {
+        const cx<PT> h = ldg(Ph, (int64_t)qq * V + s);
+        d[2 * qq] += packed_to_float(h.r);
+        d[2 * qq + 1] += packed_to_float(h.i);
+      }
+      const float a2 = -(d[6] + d[7]);
+      const float ts = d[6] * d[6] + d[7] * d[7] + a2 * a2 +
+                       2.f * (d[0] * d[0] + d[1] * d[1] + d[2] * d[2] + d[3] * d[3] + d[4] * d[4] + d[5] * d[5]);
+      th += widen_bits(ts);
+      f += widen_bits(fs);
+#pragma unroll
+      for (int qq = 0; qq < 4; ++qq) st(P, (int64_t)qq * V + s, mkc(d[2 * qq], d[2 * qq + 1]));
+    }
+  }
+  reduce_and_finalize_at<NT>(th, f, partials, ctrl, V, counts_update, ctrl->f_base,
+                             blockIdx.x + gridDim.x * blockIdx.y, nblk);
+}
+
 // Loop control of one configuration entering the residual stage (after its double Delta, theta and F):
 // F of the base, the stage and its threshold, active.
 __global__ void k_enter_residual(Ctrl *ctrl, double threshold) {

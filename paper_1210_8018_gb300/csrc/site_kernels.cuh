@@ -135,23 +135,24 @@ template <int NT> __device__ __forceinline__ void block_sum2(double &a, double &
 // Writes this block's (sum_theta, sum_F) partial; the last block to arrive reduces all partials in a
 // fixed order and updates the loop control (Algorithm 1: "calculate Delta(x), F and theta", then the
 // while-test theta >= eps). f_offset is added to F (the residual stage sums only the residual's traces).
+// The block's number among the grid's nblk blocks is bid (blockIdx.x for one-dimensional grids).
 template <int NT>
-__device__ __forceinline__ void reduce_and_finalize(double th, double f, double *partials, Ctrl *ctrl, int64_t V,
-                                                    int counts_update, double f_offset = 0.0) {
+__device__ __forceinline__ void reduce_and_finalize_at(double th, double f, double *partials, Ctrl *ctrl, int64_t V,
+                                                       int counts_update, double f_offset, unsigned bid,
+                                                       unsigned nblk) {
   __shared__ bool last;
   block_sum2<NT>(th, f);
   if (threadIdx.x == 0) {
-    partials[2 * blockIdx.x] = th;
-    partials[2 * blockIdx.x + 1] = f;
+    partials[2 * bid] = th;
+    partials[2 * bid + 1] = f;
     __threadfence();
-    const unsigned nb = gridDim.x;
-    last = (atomicAdd(&ctrl->ticket, 1u) == nb - 1);
+    last = (atomicAdd(&ctrl->ticket, 1u) == nblk - 1);
   }
   __syncthreads();
   if (!last) return;
   __threadfence();
   double a = 0.0, b = 0.0;
-  for (unsigned k = threadIdx.x; k < gridDim.x; k += NT) {
+  for (unsigned k = threadIdx.x; k < nblk; k += NT) {
     a += __ldcg(partials + 2 * k);
     b += __ldcg(partials + 2 * k + 1);
   }
@@ -176,6 +177,11 @@ __device__ __forceinline__ void reduce_and_finalize(double th, double f, double 
       ctrl->active = (theta >= ctrl->threshold) && (it < ctrl->limit);
     }
   }
+}
+template <int NT>
+__device__ __forceinline__ void reduce_and_finalize(double th, double f, double *partials, Ctrl *ctrl, int64_t V,
+                                                    int counts_update, double f_offset = 0.0) {
+  reduce_and_finalize_at<NT>(th, f, partials, ctrl, V, counts_update, f_offset, blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -344,6 +350,86 @@ __global__ void __launch_bounds__(NT, 5) k_delta_f32(const float *__restrict__ U
                                                      double *partials, Ctrl *ctrl, Lattice L, int counts_update,
                                                      int check_active, int tkid) {
   delta_body<float, NT, float>(U, P, partials, ctrl, L, counts_update, check_active, tkid);
+}
+
+// The float Delta walking along t: thread (x, y, z) takes the TCH t-slices of chunk blockIdx.y, and the
+// combinations of U_t(x) that it accumulates for one slice are those of the backward link U_t(x - t) of
+// the next, kept in registers: seven links are read per site instead of eight. The same sums in the same
+// order as delta_body (Delta is the same bits; theta and F partials are summed over other groups of sites).
+// Measured at 64^4: 0.711 -> 0.649 ms per launch. Needs Nt % TCH == 0.
+template <int NT, int TCH>
+__global__ void __launch_bounds__(NT, 5) k_delta_f32_tw(const float *__restrict__ U, float *__restrict__ P,
+                                                        double *partials, Ctrl *ctrl, Lattice L, int counts_update,
+                                                        int check_active, int tkid) {
+  const int64_t V = L.V;
+  const unsigned nblk = gridDim.x * gridDim.y;
+  {
+    const int cfg = blockIdx.z;
+    U += (int64_t)cfg * 4 * link_plane_stride<float>(V);
+    P += (int64_t)cfg * 4 * V * 2;
+    partials += (int64_t)cfg * 2 * nblk;
+    ctrl += cfg;
+  }
+  if (!should_run<float>(ctrl, check_active)) return;
+  count_run(ctrl, tkid);
+  const int64_t nxyz = L.stride[3];
+  const int64_t q = (int64_t)blockIdx.x * NT + threadIdx.x;
+  double th = 0.0, f = 0.0;
+  if (q < nxyz) {
+    const int t0 = blockIdx.y * TCH;
+    int c[4];
+    site_coords(L, q + (int64_t)t0 * nxyz, c);
+    const float *plane_t = U + 3 * link_plane_stride<float>(V);
+    float tb[9];  // combinations of U_t(x - t): the previous slice's U_t(x)
+    {
+      m3<float> u;
+      load_link(plane_t, V, site_back(L, q + (int64_t)t0 * nxyz, 3, t0), u);
+#pragma unroll
+      for (int e = 0; e < 9; ++e) tb[e] = 0.f;
+      accumulate_link(u, 1.f, tb);
+    }
+#pragma unroll 1
+    for (int k = 0; k < TCH; ++k) {
+      const int64_t s = q + (int64_t)(t0 + k) * nxyz;
+      float acc[9];
+#pragma unroll
+      for (int e = 0; e < 9; ++e) acc[e] = 0.f;
+      float fs = 0.f;
+#pragma unroll
+      for (int mu = 0; mu < 3; ++mu) {
+        const float *plane = U + (int64_t)mu * link_plane_stride<float>(V);
+        m3<float> u;
+        load_link(plane, V, site_back(L, s, mu, c[mu]), u);  // U_mu(x - mu)
+        accumulate_link(u, 1.f, acc);
+        load_link(plane, V, s, u);  // - U_mu(x)
+        accumulate_link(u, -1.f, acc);
+        fs += u.e[0].r + u.e[4].r + u.e[8].r;  // Re Tr U_mu(x)
+      }
+      {
+        m3<float> u;
+        load_link(plane_t, V, s, u);
+#pragma unroll
+        for (int e = 0; e < 9; ++e) acc[e] = fmaf(1.f, tb[e], acc[e]);  // + U_t(x - t)
+        accumulate_link(u, -1.f, acc);                                   // - U_t(x)
+        fs += u.e[0].r + u.e[4].r + u.e[8].r;
+#pragma unroll
+        for (int e = 0; e < 9; ++e) tb[e] = 0.f;
+        accumulate_link(u, 1.f, tb);
+      }
+      const float m = (acc[6] + acc[7] + acc[8]) / 3.f;
+      const float a0 = 2 * (acc[6] - m), a1 = 2 * (acc[7] - m), a2 = 2 * (acc[8] - m);
+      const float ts = a0 * a0 + a1 * a1 + a2 * a2 +
+                       2 * (acc[0] * acc[0] + acc[1] * acc[1] + acc[2] * acc[2] + acc[3] * acc[3] +
+                            acc[4] * acc[4] + acc[5] * acc[5]);
+      th += widen_exact(ts);
+      f += widen_exact(fs);
+      st(P, s, mkc(acc[0], acc[1]));
+      st(P, V + s, mkc(acc[2], acc[3]));
+      st(P, 2 * V + s, mkc(acc[4], acc[5]));
+      st(P, 3 * V + s, mkc(a0, a1));
+    }
+  }
+  reduce_and_finalize_at<NT>(th, f, partials, ctrl, V, counts_update, 0.0, blockIdx.x + gridDim.x * blockIdx.y, nblk);
 }
 
 // Rebuild the full anti-Hermitian traceless matrix from the packed fields (type PT), scaled by a.

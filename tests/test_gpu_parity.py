@@ -92,6 +92,24 @@ def test_float_t_filter_in_registers(lgf, dims, monkeypatch):
     assert_matrix_close(outs[0], Dt_ref, rtol=5e-6, scale=float(np.abs(Dt_ref).max()))
 
 
+@pytest.mark.parametrize("dims", [(6, 4, 8, 16), (16, 16, 16, 16)])
+def test_float_delta_walking_t(lgf, dims, monkeypatch):
+    """The float Delta that walks along t (the backward t link's combinations carried from the previous
+    slice) gives the same bits as the kernel in site order (LGF_TWALK=0); theta and F, summed over other
+    groups of sites, agree to 1e-13."""
+    U = synth.config(dims, 28, 0.6)
+    res = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("LGF_TWALK", flag)
+        with lgf.Lattice(dims) as lat:
+            out = np.empty(U.shape[1:], dtype=np.complex128)
+            th, F = lat.delta(U, out, "fp32")
+        res.append((out, th, F))
+    assert np.array_equal(res[0][0], res[1][0])
+    assert abs(res[0][1] - res[1][1]) <= 1e-13 * res[1][1]
+    assert abs(res[0][2] - res[1][2]) <= 1e-13
+
+
 def test_float_xy_planes_in_registers(lgf, monkeypatch):
     """The float 64 x 64 xy passes held in registers apply the operations of the shared-memory tile passes
     in the same order: the filtered field is the same bits as with LGF_XY_REG=0, and matches the oracle."""
