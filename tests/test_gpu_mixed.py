@@ -82,6 +82,27 @@ def test_mixed_store_mid_float_stage_is_gauge_equivalent(lgf):
     assert oracle.theta(oracle.delta(Us)) < 0.5 * th0
 
 
+def test_t_walking_kernels_match_site_order(lgf, monkeypatch):
+    """Mixed fixes with the float and residual Delta and updates walking along t (8 slices per thread,
+    forced at 16^4 with LGF_TWALK_MIN_BLOCKS=0) against the site-order kernels (LGF_TWALK=0): the same
+    iterations, F to 1e-14 and the links to 1e-12 (theta, summed over other groups of sites, may decide a
+    stage switch at another rounding)."""
+    monkeypatch.setenv("LGF_TWALK_MIN_BLOCKS", "0")
+    dims = (16, 16, 16, 16)
+    U = synth.config(dims, 8, 0.6)
+    res = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("LGF_TWALK", flag)
+        Uf = U.copy()
+        with lgf.Lattice(dims) as lat:
+            r = lat.fix(Uf, 0.08, 1e-15, "mixed", max_iter=400)
+        res.append((r, Uf))
+    (r1, U1), (r0, U0) = res
+    assert r1["converged"] and r0["converged"] and r1["iters"] == r0["iters"]
+    assert abs(r1["F"] - r0["F"]) < 1e-14
+    assert float(np.abs(U1 - U0).max()) < 1e-12
+
+
 def test_mixed_float_stage_hands_over_when_theta_stalls(lgf):
     """A switch point below what float links resolve: the float stage stops lowering theta, hands over on
     its own, and the double stage converges with the links still gauge-equivalent to the input."""

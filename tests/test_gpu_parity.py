@@ -95,8 +95,9 @@ def test_float_t_filter_in_registers(lgf, dims, monkeypatch):
 @pytest.mark.parametrize("dims", [(6, 4, 8, 16), (16, 16, 16, 16)])
 def test_float_delta_walking_t(lgf, dims, monkeypatch):
     """The float Delta that walks along t (the backward t link's combinations carried from the previous
-    slice) gives the same bits as the kernel in site order (LGF_TWALK=0); theta and F, summed over other
-    groups of sites, agree to 1e-13."""
+    slice; forced on these small lattices with LGF_TWALK_MIN_BLOCKS=0) gives the same bits as the kernel in
+    site order (LGF_TWALK=0); theta and F, summed over other groups of sites, agree to 1e-13."""
+    monkeypatch.setenv("LGF_TWALK_MIN_BLOCKS", "0")
     U = synth.config(dims, 28, 0.6)
     res = []
     for flag in ("1", "0"):
