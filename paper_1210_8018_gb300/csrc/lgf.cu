@@ -151,7 +151,7 @@ struct lgf_ctx {
   bool fft_persist = true;   // specialised FFT passes as one wave of tile-looping blocks (LGF_FFT_PERSIST=0: off)
   bool tfilter_reg = true;   // float t pass with the filter in registers at Nt = 64 (LGF_TFILTER_REG=0: off)
   bool xy_reg = true;        // float 64 x 64 xy passes in registers (LGF_XY_REG=0: off)
-  bool twalk = true;  // float and residual Delta and updates walking along t (LGF_TWALK=0: off; twalk_chunk)
+  bool twalk = true;  // float and residual Delta and updates walking along t (LGF_TWALK=0: off; twalk_on)
   int64_t twalk_min_blocks = 2048;  // LGF_TWALK_MIN_BLOCKS
   int handover_split[2] = {2, 2};  // links per site in FP64 (even, odd warps), the rest in fixed point
   int update_split[2] = {2, 2};    // the same for the general (large-step) form of the double update
@@ -541,7 +541,7 @@ lgf_status ensure_common(lgf_ctx *ctx) {
   if (!ctx->partials) {
     ctx->nblocks_site = (int)((ctx->V + NT * kSitesPerThread - 1) / (NT * kSitesPerThread));
     // one (theta, F) pair per block of the largest reducing grid: the site kernels' nblocks_site, or the
-    // t-walking kernels' columns x Nt / 8 blocks (twalk_chunk)
+    // t-walking kernels' columns x Nt / 8 blocks (twalk_on)
     ctx->partials_blocks = std::max<int64_t>(
         std::max(ctx->nblocks_site, 1), (ctx->L.stride[3] + NT - 1) / NT * std::max(ctx->n[3] / 8, 1));
     CK(cudaMalloc(&ctx->partials, sizeof(double) * 2 * (size_t)ctx->partials_blocks * ctx->nb));
@@ -613,19 +613,19 @@ lgf_status output_ptr(lgf_ctx *ctx, double *p, size_t bytes, double **buf, size_
 
 unsigned grid1(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
-// Slices per thread of the kernels that walk along t: 8 when Nt allows and the launch still has
-// twalk_min_blocks blocks, else 0 (site order). Measured: at 64^4 (8192 blocks) the walking kernels save the
-// second read of each t-neighbour and 9 ms per mixed fix; on single lattices with fewer blocks (32^4: 512,
-// 32^3 x 64: 1024) the second read hits L2 anyway and the site-order kernels are as fast or faster (32^3 x 64:
-// 28.5 against 29.5 ms); shorter walks (4 or 2 slices) were slower still.
-int twalk_chunk(const lgf_ctx *ctx) {
-  if (!ctx->twalk || ctx->n[3] % 8) return 0;
-  const int64_t blocks = (int64_t)grid1(ctx->L.stride[3], NT) * (ctx->n[3] / 8);  // per configuration
-  return blocks * ctx->nb >= ctx->twalk_min_blocks && blocks <= ctx->partials_blocks ? 8 : 0;
+// The kernels that walk along t give each thread kTwalkSlices consecutive t-slices. They run when Nt allows
+// and the launch still has twalk_min_blocks blocks; otherwise the site-order kernels run. Measured: at 64^4
+// (8192 blocks) the walking kernels save the second read of each t-neighbour and 9 ms per mixed fix; on
+// single lattices with fewer blocks (32^4: 512, 32^3 x 64: 1024) the second read hits L2 anyway and the
+// site-order kernels are as fast or faster (32^3 x 64: 28.5 against 29.5 ms); shorter walks (4 or 2 slices,
+// more blocks) were slower still.
+constexpr int kTwalkSlices = 8;
+bool twalk_on(const lgf_ctx *ctx) {
+  if (!ctx->twalk || ctx->n[3] % kTwalkSlices) return false;
+  const int64_t blocks = (int64_t)grid1(ctx->L.stride[3], NT) * (ctx->n[3] / kTwalkSlices);  // per configuration
+  return blocks * ctx->nb >= ctx->twalk_min_blocks && blocks <= ctx->partials_blocks;
 }
-template <typename F> void with_chunk(int tch, F &&f) {
-  if (tch == 8) f(std::integral_constant<int, 8>());
-}
+dim3 twalk_grid(const lgf_ctx *ctx) { return dim3(grid1(ctx->L.stride[3], NT), ctx->n[3] / kTwalkSlices, ctx->nb); }
 
 template <typename T> lgf_status launch_delta(lgf_ctx *ctx, State<T> &S, int counts_update, int check_active) {
   TRY(timed_begin(ctx, kid<T>(KID_DELTA)));
@@ -634,12 +634,9 @@ template <typename T> lgf_status launch_delta(lgf_ctx *ctx, State<T> &S, int cou
     const dim3 grid(ctx->nblocks_site, 1, ctx->nb);
     FT *P = reinterpret_cast<FT *>(S.P);
     if constexpr (std::is_same<T, float>::value) {
-      if (const int tch = twalk_chunk(ctx))
-        with_chunk(tch, [&](auto c) {
-          constexpr int TCH = decltype(c)::value;
-          k_delta_f32_tw<NT, TCH><<<dim3(grid1(ctx->L.stride[3], NT), ctx->n[3] / TCH, ctx->nb), NT, 0, ctx->stream>>>(
-              S.U, P, ctx->partials, ctx->ctrl, ctx->L, counts_update, check_active, kid<T>(KID_DELTA));
-        });
+      if (twalk_on(ctx))
+        k_delta_f32_tw<NT, kTwalkSlices><<<twalk_grid(ctx), NT, 0, ctx->stream>>>(
+            S.U, P, ctx->partials, ctx->ctrl, ctx->L, counts_update, check_active, kid<T>(KID_DELTA));
       else
         k_delta_f32<NT><<<grid, NT, 0, ctx->stream>>>(S.U, P, ctx->partials, ctx->ctrl, ctx->L, counts_update,
                                                       check_active, kid<T>(KID_DELTA));
@@ -758,18 +755,17 @@ lgf_status launch_iteration_float(lgf_ctx *ctx, double alpha, bool reunit) {
   TRY(timed_begin(ctx, kidx));
   const dim3 grid(grid1(ctx->V, NT), 1, ctx->nb);
   const float ha = (float)(0.5 * alpha);
-  auto walk = [&](auto tch) {
-    constexpr int TCH = decltype(tch)::value;
-    const dim3 gtw(grid1(ctx->L.stride[3], NT), ctx->n[3] / TCH, ctx->nb);
+  if (twalk_on(ctx)) {
+    constexpr int TCH = kTwalkSlices;
     if (reunit && ctx->reunit_fp64)
-      k_update_fused_f32_tw<NT, 2, TCH><<<gtw, NT, 0, ctx->stream>>>(S.U, S.P, ctx->Gacc, ha, ctx->L, ctx->ctrl, kidx);
+      k_update_fused_f32_tw<NT, 2, TCH><<<twalk_grid(ctx), NT, 0, ctx->stream>>>(S.U, S.P, ctx->Gacc, ha, ctx->L,
+                                                                                 ctx->ctrl, kidx);
     else if (reunit)
-      k_update_fused_f32_tw<NT, 1, TCH><<<gtw, NT, 0, ctx->stream>>>(S.U, S.P, ctx->Gacc, ha, ctx->L, ctx->ctrl, kidx);
+      k_update_fused_f32_tw<NT, 1, TCH><<<twalk_grid(ctx), NT, 0, ctx->stream>>>(S.U, S.P, ctx->Gacc, ha, ctx->L,
+                                                                                 ctx->ctrl, kidx);
     else
-      k_update_fused_f32_tw<NT, 0, TCH><<<gtw, NT, 0, ctx->stream>>>(S.U, S.P, ctx->Gacc, ha, ctx->L, ctx->ctrl, kidx);
-  };
-  if (const int tch = twalk_chunk(ctx)) {
-    with_chunk(tch, walk);
+      k_update_fused_f32_tw<NT, 0, TCH><<<twalk_grid(ctx), NT, 0, ctx->stream>>>(S.U, S.P, ctx->Gacc, ha, ctx->L,
+                                                                                 ctx->ctrl, kidx);
   } else if (reunit && ctx->reunit_fp64)
     k_update_fused_f32<NT, 2><<<grid, NT, 0, ctx->stream>>>(S.U, S.P, ctx->Gacc, ha, ctx->L, ctx->ctrl, kidx);
   else if (reunit)
@@ -828,14 +824,10 @@ lgf_status launch_delta_residual(lgf_ctx *ctx, int counts_update) {
   TRY(timed_begin(ctx, kid<float>(KID_DELTA_RESIDUAL)));
   TRY(with_fft_type<double>(ctx, [&](auto tag) -> lgf_status {
     using FT = decltype(tag);
-    if (const int tch = twalk_chunk(ctx))
-      with_chunk(tch, [&](auto c) {
-        constexpr int TCH = decltype(c)::value;
-        k_delta_residual_tw<NT, FT, TCH><<<dim3(grid1(ctx->L.stride[3], NT), ctx->n[3] / TCH, ctx->nb), NT, 0,
-                                           ctx->stream>>>(ctx->Rres, reinterpret_cast<const FT *>(ctx->s64.P),
-                                                          ctx->s32.P, ctx->partials, ctx->ctrl, ctx->L, counts_update,
-                                                          kid<float>(KID_DELTA_RESIDUAL));
-      });
+    if (twalk_on(ctx))
+      k_delta_residual_tw<NT, FT, kTwalkSlices><<<twalk_grid(ctx), NT, 0, ctx->stream>>>(
+          ctx->Rres, reinterpret_cast<const FT *>(ctx->s64.P), ctx->s32.P, ctx->partials, ctx->ctrl, ctx->L,
+          counts_update, kid<float>(KID_DELTA_RESIDUAL));
     else
       k_delta_residual<NT, FT><<<dim3(ctx->nblocks_site, 1, ctx->nb), NT, 0, ctx->stream>>>(
           ctx->Rres, reinterpret_cast<const FT *>(ctx->s64.P), ctx->s32.P, ctx->partials, ctx->ctrl, ctx->L,
@@ -875,14 +867,10 @@ lgf_status residual_begin(lgf_ctx *ctx) {
 lgf_status launch_iteration_residual(lgf_ctx *ctx, double alpha) {
   TRY(launch_filter<float>(ctx, ctx->s32, ctx->s32.P, 3));
   TRY(timed_begin(ctx, kid<float>(KID_UPDATE_RESIDUAL)));
-  if (const int tch = twalk_chunk(ctx))
-    with_chunk(tch, [&](auto c) {
-      constexpr int TCH = decltype(c)::value;
-      k_update_residual_tw<NT, TCH><<<dim3(grid1(ctx->L.stride[3], NT), ctx->n[3] / TCH, ctx->nb), NT, 0,
-                                      ctx->stream>>>(ctx->s32.U, ctx->Rres, ctx->Kres, ctx->s32.P,
-                                                     (float)(0.5 * alpha), ctx->L, ctx->ctrl,
-                                                     kid<float>(KID_UPDATE_RESIDUAL));
-    });
+  if (twalk_on(ctx))
+    k_update_residual_tw<NT, kTwalkSlices><<<twalk_grid(ctx), NT, 0, ctx->stream>>>(
+        ctx->s32.U, ctx->Rres, ctx->Kres, ctx->s32.P, (float)(0.5 * alpha), ctx->L, ctx->ctrl,
+        kid<float>(KID_UPDATE_RESIDUAL));
   else
     k_update_residual<NT><<<dim3(grid1(ctx->V, NT), 1, ctx->nb), NT, 0, ctx->stream>>>(
         ctx->s32.U, ctx->Rres, ctx->Kres, ctx->s32.P, (float)(0.5 * alpha), ctx->L, ctx->ctrl,
